@@ -1,0 +1,160 @@
+"""ctypes wrapper of the CPU oracle (hobo_oracle.c).
+
+Test infrastructure only: the tests, the package smoke check and the
+benchmark's CPU-baseline leg may import this module; the product path never
+does.  Everything here is a thin marshalling layer over the C routines,
+which state the arithmetic and its sources.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hobo_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fno-strict-aliasing",
+           "-shared", "-fPIC"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/liboracle.so (gcc, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", *_CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.c_void_p
+        i64, i32, u64, dbl, flt = C.c_int64, C.c_int, C.c_uint64, C.c_double, C.c_float
+        _lib.orc_energy.restype = dbl
+        _lib.orc_energy.argtypes = [P, P, i64, i32, P]
+        _lib.orc_energy_batch.argtypes = [P, P, i64, i32, i32, P, i64, P]
+        _lib.orc_energy_batch_i64.argtypes = [P, P, i64, i32, i32, P, i64, P]
+        _lib.orc_bruteforce.argtypes = [P, P, i64, i32, i32, P]
+        _lib.orc_flip_delta.argtypes = [P, P, i64, i32, i32, P, P]
+        _lib.orc_fields.argtypes = [P, P, i64, i32, i32, P, P]
+        _lib.orc_philox4x32_10.argtypes = [P, P, P]
+        _lib.orc_exp2.restype = flt
+        _lib.orc_exp2.argtypes = [flt]
+        _lib.orc_metropolis.restype = i32
+        _lib.orc_metropolis.argtypes = [flt, flt, C.c_uint32]
+        _lib.orc_init_states.argtypes = [u64, i32, i64, P]
+        _lib.orc_anneal.argtypes = [P, P, i64, i32, i32, u64, i64, i64, P, i32,
+                                    P, P, P, P, P, i64, P]
+        _lib.orc_anneal_naive.argtypes = [P, P, i64, i32, i32, u64, i64, i64, P, i32,
+                                          P, P, P, P, P]
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _terms(inst):
+    idx = np.ascontiguousarray(inst.idx, dtype=np.int32)
+    coef = np.ascontiguousarray(inst.coef, dtype=np.float64)
+    return idx, coef
+
+
+def energy(inst, X: np.ndarray) -> np.ndarray:
+    """Energies (float64) of the 0/1 states in rows of X (uint8 [B, N])."""
+    idx, coef = _terms(inst)
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    E = np.zeros(X.shape[0], dtype=np.float64)
+    lib().orc_energy_batch(_p(idx), _p(coef), idx.shape[0], inst.order, inst.N, _p(X), X.shape[0], _p(E))
+    return E
+
+
+def energy_int(inst, X: np.ndarray) -> np.ndarray:
+    """Exact int64 energies for integer-coefficient instances."""
+    idx, coef = _terms(inst)
+    ci = np.ascontiguousarray(np.rint(coef).astype(np.int64))
+    if not np.array_equal(ci.astype(np.float64), coef):
+        raise ValueError("instance has non-integer coefficients")
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    E = np.zeros(X.shape[0], dtype=np.int64)
+    lib().orc_energy_batch_i64(_p(idx), _p(ci), idx.shape[0], inst.order, inst.N, _p(X), X.shape[0], _p(E))
+    return E
+
+
+def bruteforce(inst) -> np.ndarray:
+    """Energy of every state s in [0, 2^N), x_i = bit i of s."""
+    if inst.N > 30:
+        raise ValueError("N too large for enumeration")
+    idx, coef = _terms(inst)
+    E = np.zeros(1 << inst.N, dtype=np.float64)
+    lib().orc_bruteforce(_p(idx), _p(coef), idx.shape[0], inst.order, inst.N, _p(E))
+    return E
+
+
+def flip_delta(inst, x: np.ndarray) -> np.ndarray:
+    idx, coef = _terms(inst)
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    d = np.zeros(inst.N, dtype=np.float64)
+    lib().orc_flip_delta(_p(idx), _p(coef), idx.shape[0], inst.order, inst.N, _p(x), _p(d))
+    return d
+
+
+def fields(inst, x: np.ndarray) -> np.ndarray:
+    idx, coef = _terms(inst)
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    g = np.zeros(inst.N, dtype=np.float64)
+    lib().orc_fields(_p(idx), _p(coef), idx.shape[0], inst.order, inst.N, _p(x), _p(g))
+    return g
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(np.array(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.array(key, dtype=np.uint32))
+    o = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(o))
+    return o
+
+
+def exp2(t: float) -> np.float32:
+    return np.float32(lib().orc_exp2(float(np.float32(t))))
+
+
+def metropolis(dE: float, beta: float, w: int) -> bool:
+    return bool(lib().orc_metropolis(float(np.float32(dE)), float(np.float32(beta)), int(w) & 0xFFFFFFFF))
+
+
+def init_states(seed: int, N: int, B: int) -> np.ndarray:
+    X = np.zeros((B, N), dtype=np.uint8)
+    lib().orc_init_states(seed, N, B, _p(X))
+    return X
+
+
+def anneal(inst, seed: int, B: int, betas: np.ndarray, state0: int = 0, rec_B: int = 0,
+           naive: bool = False) -> dict:
+    """Run the oracle annealer on states state0 .. state0+B-1."""
+    idx, coef = _terms(inst)
+    betas = np.ascontiguousarray(betas, dtype=np.float32)
+    S = betas.shape[0]
+    N = inst.N
+    Xf = np.zeros((B, N), np.uint8)
+    Xb = np.zeros((B, N), np.uint8)
+    Ef = np.zeros(B, np.float64)
+    Eb = np.zeros(B, np.float64)
+    acc = np.zeros(B, np.int64)
+    if naive:
+        lib().orc_anneal_naive(_p(idx), _p(coef), idx.shape[0], inst.order, N, seed, state0, B,
+                               _p(betas), S, _p(Xf), _p(Ef), _p(Xb), _p(Eb), _p(acc))
+        return dict(X=Xf, E=Ef, bestX=Xb, bestE=Eb, accepts=acc)
+    rec = np.zeros((S, rec_B, N), np.uint8) if rec_B > 0 else None
+    lib().orc_anneal(_p(idx), _p(coef), idx.shape[0], inst.order, N, seed, state0, B,
+                     _p(betas), S, _p(Xf), _p(Ef), _p(Xb), _p(Eb), _p(acc), rec_B,
+                     _p(rec) if rec is not None else None)
+    return dict(X=Xf, E=Ef, bestX=Xb, bestE=Eb, accepts=acc, rec=rec)
