@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Benchmark of the batched HOBO annealer on one GB300 (or N, as replicas).
+
+Workload (one step = one pass of the whole hot path): the dense order-3
+HOBO with N=256 variables and every i<=j<=k coefficient ~ N(0,1) float32
+(2,829,056 tensor entries), B=4096 states, 1000 sweeps of a geometric
+temperature schedule 10 -> 0.01.  A step is one hobo_anneal call: Philox
+initial states, the energy/field contraction, the Metropolis sweep kernel,
+and the float64 re-score of the best states.
+
+metric: attempted single-bit flip updates per second (B * N * sweeps per
+step), whole job.  Inputs (instance, schedule) are resident in HBM when the
+timed region starts; L2 is flushed (256 MiB write) between timed steps.
+
+--impl reference times the CPU oracle (the plain statement of the method)
+on the host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "bit-flip updates/s (attempted single-bit Metropolis flips), dense order-3 N=256 HOBO, B=4096, 1000 sweeps"
+UNIT = "flips/s"
+WORKLOAD = "dense_float"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="tuned", choices=["tuned", "plain"])
+    ap.add_argument("--cpu-states", type=int, default=8, help="oracle sample size (states)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    inst = W.dense_float(2)
+    T0, T1, S, B = W.SCHEDULES[WORKLOAD]
+    return inst, W.geometric_betas(T0, T1, S), B, S
+
+
+def cpu_oracle_rate(inst, betas, states: int, state0: int = 0):
+    """Oracle annealer on `states` states of the workload (single thread)."""
+    from oracle import oracle as O
+    O.lib()
+    t = time.perf_counter()
+    O.anneal(inst, 2, states, betas, state0=state0)
+    dt = time.perf_counter() - t
+    return states * inst.N * len(betas) / dt, dt
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, dev_id: str, path: str | None):
+        self.dev_id, self.path, self.proc = dev_id, path, None
+
+    def __enter__(self):
+        try:
+            self.out = open(self.path, "w") if self.path else subprocess.DEVNULL
+            self.tmp = self.path or os.devnull
+            self.buf = open(self.path + ".raw", "w") if self.path else None
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.dev_id, "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+            if self.path:
+                with open(self.path, "w") as f:
+                    f.write("\n".join(self.lines) + "\n")
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = float(p[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id(torch, local):
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[local] if vis else str(local)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    inst, betas, B, S = workload()
+    n = max(1, a.cpu_states // 4)
+    for _ in range(max(0, min(a.warmup, 1))):
+        cpu_oracle_rate(inst, betas[:50], 1)
+    times = []
+    for k in range(a.steps):
+        _, dt = cpu_oracle_rate(inst, betas, n, state0=k * n)
+        times.append(dt)
+    flips = n * inst.N * S
+    ms = 1000.0 * statistics.mean(times)
+    v = flips / (ms / 1000.0)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: order 3, N=256, all i<=j<=k entries N(0,1), "
+                                   f"1000 sweeps T 10->0.01; sample of {n} states per step",
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n} states x {S} sweeps x N=256 per step (oracle, 1 thread)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2407_19987_gb300 as H
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    inst, betas, B, S = workload()
+    h = H.Instance.from_terms(inst.idx, inst.coef, inst.N)
+    info = h.info()
+    mode = H.HOBO_ANNEAL_TUNED if a.mode == "tuned" else H.HOBO_ANNEAL_PLAIN
+    seed = 2 + 1_000_003 * rank          # each rank anneals its own B states (weak scaling)
+    W_ = h.W
+    bestX = torch.zeros((B, W_), dtype=torch.int32, device=dev)
+    bestE32 = torch.empty(B, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    acc = torch.zeros(B, dtype=torch.int64, device=dev)
+
+    def step(events=None, accepts=False):
+        return h.anneal(seed, B, betas, mode=mode, bestX=bestX, bestE32=bestE32,
+                        want_accepts=accepts, sweep_events=events)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    # accepted flips of one step (same seed -> same trajectory every step)
+    r = step(accepts=True)
+    torch.cuda.synchronize()
+    accepts = int(r["accepts"].sum().item())
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    clocks_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with ClockSampler(gpu_id(torch, local), clocks_path) as cs:
+        for k in range(a.steps):
+            flush.fill_(float(k))                 # evict L2 between timed steps (not timed)
+            ev[k][0].record()
+            step(events=sev[k])
+            ev[k][1].record()
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    sweep_ms = [e0.elapsed_time(e1) for e0, e1 in sev]
+    ms = statistics.mean(step_ms)
+    sweep_avg = statistics.mean(sweep_ms)
+    if world > 1:
+        t = torch.tensor([ms, sweep_avg], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, sweep_avg = float(t[0]), float(t[1])
+    flips_step = B * inst.N * S
+    value = world * flips_step / (ms / 1000.0)
+
+    # ---- end to end through the C ABI with host buffers ------------------
+    pin_beta = torch.from_numpy(betas.copy()).pin_memory()
+    hX = torch.empty((B, W_), dtype=torch.int32).pin_memory()
+    hE = torch.empty(B, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(max(2, a.steps)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        rr = h.anneal(seed, B, pin_beta.numpy(), mode=mode, bestX=bestX, bestE32=bestE32)
+        hX.copy_(rr["bestX"], non_blocking=True)
+        hE.copy_(rr["bestE"], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1000.0 * (time.perf_counter() - t))
+    e2e_v = world * flips_step / (statistics.mean(e2e_ms) / 1000.0)
+    h2d = betas.nbytes
+    d2h = hX.numel() * 4 + hE.numel() * 8
+
+    pk, pk_kind = peaks()
+    # dense sweep: each accepted flip of bit i reads the set rows of the
+    # (N x P) float32 slab S3[i] (about N/2 rows) plus the S2 row.
+    P = (inst.N + 3) & ~3
+    bytes_sweep = accepts * (inst.N / 2 + 1) * P * 4 + B * (inst.N * 4 + 2 * W_ * 4 * 2 + 16)
+    achieved = bytes_sweep / (sweep_avg / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: order 3, N=256, all i<=j<=k entries N(0,1) f32, "
+                               f"B={B} states per GPU, {S} sweeps, geometric T 10->0.01",
+                   "mode": a.mode, "dense_layout": info["dense"], "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": f"replicas x{world} (independent states per GPU)",
+                   "accepted_flips_per_step": accepts, "sweep_kernel_ms": sweep_avg},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "kernel": "sweep_tuned_kernel (dense)", "peak_kind": pk_kind},
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 4 * a.steps,
+        "wall_s_timed": wall,
+    }
+    cl = cs.summary()
+    if cl:
+        line["clocks"] = cl
+    if rank == 0 and not a.no_cpu_baseline:
+        rate, dt = cpu_oracle_rate(inst, betas, a.cpu_states)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{a.cpu_states} states x {S} sweeps x N=256 ({dt:.1f} s, 1 thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * hobo.h -- C ABI of the GB300 HOBO contraction and annealing library.
+ *
+ * The library evaluates higher-order binary objectives stored as an order-k
+ * HOBO tensor (arXiv 2407.19987, Sec. II.B-C) for a batch of binary states
+ * (the tensor batch system of Sec. IV.C), and runs batched simulated
+ * annealing over them (Sec. II.D.1).  All compute runs in the library's own
+ * CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: HOBO_OK (0) or a negative HOBO_ERR_* code.  Nothing
+ *    throws across the ABI.  hobo_last_error() returns a thread-local
+ *    message describing the most recent failure on the calling thread.
+ *  - Packed states: a state of N bits is W = ceil(N/32) uint32 words; bit i
+ *    is bit (i % 32) of word (i / 32).  Bits at positions >= N in the last
+ *    word are ignored on input and written as 0.
+ *  - Device pointers are CUDA device (or managed) memory on the current
+ *    device; host pointers are ordinary host memory.  The caller owns every
+ *    buffer it passes; the library never frees or retains them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued asynchronously on it; host arrays passed
+ *    to an entry point may be reused as soon as the call returns.
+ *  - Energies exclude the constant term of the objective (the "offset" the
+ *    paper's listings print, Sec. V): objective = energy + offset.
+ */
+#ifndef HOBO_H
+#define HOBO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define HOBO_OK               0
+#define HOBO_ERR_ARG         -1   /* null pointer, bad size, index out of range */
+#define HOBO_ERR_ORDER       -2   /* order outside 1..HOBO_MAX_ORDER */
+#define HOBO_ERR_NOT_EXACT   -3   /* HOBO_INTEGER requested but coefficients are
+                                     not integers or sum |c| >= 2^24 */
+#define HOBO_ERR_OOM         -4   /* device or host allocation failed */
+#define HOBO_ERR_CUDA        -5   /* a CUDA runtime call failed */
+#define HOBO_ERR_TIMEOUT     -6   /* a bounded device-side wait gave up */
+#define HOBO_ERR_UNSUPPORTED -7   /* valid request this build does not cover */
+
+#define HOBO_MAX_ORDER 8
+#define HOBO_MAX_N     1024       /* variables per instance */
+
+/* ---- creation flags -------------------------------------------------- */
+#define HOBO_INTEGER      1u  /* require the bit-exact integer path: every folded
+                                 coefficient an integer and sum |c| < 2^24, so
+                                 every float32 partial sum is exact */
+#define HOBO_FORCE_SPARSE 2u  /* use the term-list layouts even if dense */
+#define HOBO_FORCE_DENSE  4u  /* build the dense slab layout (order <= 3) */
+#define HOBO_SPLIT3       8u  /* tensor-core energy: hi+mid+lo bf16 split
+                                 (exact for float32 coefficients) instead of
+                                 hi+lo */
+
+typedef struct hobo_instance* hobo_h;
+
+/*
+ * hobo_create -- build an instance from a dense order-k tensor.
+ *   T      host, float32, N^order entries, row-major (last index fastest).
+ *          Any entry may be nonzero: an entry at index tuple t contributes
+ *          T[t] * prod_{i in t} x_i.  Since x_i^2 = x_i for binary x, every
+ *          entry is folded onto the distinct set of its indices (the
+ *          replicate-smallest storage of Sec. III.C / IV.A is one case;
+ *          entries below the diagonal are accepted too).
+ *   order  1..HOBO_MAX_ORDER;  N 1..HOBO_MAX_N.
+ *   flags  HOBO_* creation flags.
+ * The tensor is copied; the caller keeps ownership of T.  Uses the current
+ * CUDA device; synchronous.  N^order must fit in int64.
+ * Errors: HOBO_ERR_ARG, HOBO_ERR_ORDER, HOBO_ERR_NOT_EXACT, HOBO_ERR_OOM,
+ * HOBO_ERR_CUDA.  On error *out is set to NULL.
+ */
+int hobo_create(hobo_h* out, const float* T, int order, int N, unsigned flags);
+
+/*
+ * hobo_create_terms -- build an instance from tensor entries (Sec. II.C):
+ *   idx   host int32 [nnz][order], each index in [0, N)
+ *   coef  host float32 [nnz]
+ * Entries with the same distinct index set are added (x^2 = x).  Same
+ * ownership, flags and errors as hobo_create.
+ */
+int hobo_create_terms(hobo_h* out, const int32_t* idx, const float* coef, int64_t nnz,
+                      int order, int N, unsigned flags);
+
+/* Release an instance and all device memory it owns.  NULL is a no-op.
+ * The caller must make sure no work using it is still in flight. */
+void hobo_destroy(hobo_h h);
+
+/* Static description of an instance (host-side, no GPU work). */
+typedef struct {
+    int N;                 /* variables */
+    int order;             /* tensor order k */
+    int words;             /* W = ceil(N/32) */
+    int dense;             /* 1 if the dense slab layout is used */
+    int integer;           /* 1 if all folded coefficients are integers and
+                              sum |c| < 2^24 (bit-exact float32 path) */
+    int64_t terms[HOBO_MAX_ORDER + 1];  /* folded monomials per degree */
+    double abs_sum;        /* sum of |folded coefficient| */
+} hobo_info_t;
+
+int hobo_info(hobo_h h, hobo_info_t* info);
+
+/*
+ * hobo_energy -- batched contraction (Sec. IV.C): for each of B states,
+ *   E[b]      = sum over folded monomials S of c_S * prod_{i in S} x_bi
+ *   dE[b*N+i] = E(x_b with bit i flipped) - E(x_b) = (1 - 2 x_bi) g_bi,
+ *               g_bi the local field dE/dx_i of the multilinear form.
+ *   X   device uint32 [B][W] packed states
+ *   E   device float32 [B]
+ *   dE  device float32 [B][N], or NULL to skip the flip deltas
+ * Dense order-3 instances run the tcgen05 tensor-core contraction
+ * (tensor reshaped to (N^2 x N) against the bit matrix, bf16 split of the
+ * coefficients, float32 accumulation); others the term-list kernel.
+ * Integer instances give exact results.  B >= 0 (B = 0 is a no-op).
+ * Errors: HOBO_ERR_ARG, HOBO_ERR_CUDA.
+ */
+int hobo_energy(hobo_h h, const uint32_t* X, int B, float* E, float* dE, void* stream);
+
+/* hobo_energy with an explicit contraction path:
+ *   path 0 = automatic, 1 = term-list kernel (CUDA cores, float32),
+ *   path 2 = tcgen05 tensor-core kernel (dense order-3 instances only;
+ *            HOBO_ERR_UNSUPPORTED otherwise). */
+int hobo_energy_path(hobo_h h, const uint32_t* X, int B, float* E, float* dE, int path,
+                     void* stream);
+
+/*
+ * hobo_energy_fp64 -- the energies of B packed states summed in float64
+ * over the folded coefficients (kept in float64), for re-scoring reported
+ * states.  X device uint32 [B][W]; E device double [B].
+ */
+int hobo_energy_fp64(hobo_h h, const uint32_t* X, int B, double* E, void* stream);
+
+/* ---- annealing -------------------------------------------------------- */
+
+#define HOBO_ANNEAL_TUNED  0  /* persistent kernel, states in shared memory */
+#define HOBO_ANNEAL_PLAIN  1  /* one thread per state, fields in global memory */
+
+typedef struct {
+    int mode;              /* HOBO_ANNEAL_TUNED or HOBO_ANNEAL_PLAIN */
+    int states_per_block;  /* tuned mode: 1..32 states per CTA, 0 = automatic */
+    int sweep0;            /* index of the first sweep in the random stream
+                              (resume: the number of sweeps already run) */
+    int resume;            /* 1: start from X_io / bestX / bestE32_io instead of
+                              the random initial states */
+    uint32_t* X_io;        /* device [B][W] or NULL: start states when resume,
+                              final states on return */
+    float* bestE32_io;     /* device [B] or NULL: float32 best energy tracked
+                              during the run (in when resume, out always) */
+    float* E_io;           /* device [B] or NULL: final float32 energies on
+                              return; with resume and g_io, the energies of
+                              X_io to continue from */
+    float* g_io;           /* device [B][N] or NULL: final float32 local fields
+                              on return; with resume and E_io, the fields to
+                              continue from (bit-exact continuation of a
+                              float instance; without them fields and
+                              energies are recomputed from X_io) */
+    int64_t* accepts;      /* device [B] or NULL: accepted flips (added to) */
+    void* ev_sweep_begin;  /* cudaEvent_t or NULL: recorded on `stream` right
+                              before the sweep kernel is enqueued */
+    void* ev_sweep_end;    /* cudaEvent_t or NULL: recorded right after it */
+} hobo_anneal_opts;
+
+/*
+ * hobo_anneal -- batched Metropolis simulated annealing (Sec. II.D.1) of B
+ * independent states.
+ *   seed    64-bit key of the counter-based Philox4x32-10 stream.  The draw
+ *           for (state b, sweep s, bit i) uses counter (i/4, s, b, 0),
+ *           word i%4; initial bit i of state b uses counter (i/4, 0, b, 1),
+ *           bit 31 of word i%4.  Results do not depend on the launch shape.
+ *   beta    host float32 [sweeps], inverse temperature of each sweep.
+ *   Each sweep visits bits 0..N-1 in order; a flip with delta dE is
+ *   accepted iff dE <= 0 or u < exp2(-(beta*dE)*log2 e), u = (w>>8)*2^-24,
+ *   where exp2 is the library's fixed float sequence (range reduction to
+ *   [-0.5,0.5], degree-6 Taylor polynomial; 0 below -125).  Fields are
+ *   updated incrementally after each accepted flip.
+ *   bestX   device uint32 [B][W]: lowest-energy state seen by each state
+ *           (strict improvement; in/out when opts->resume)
+ *   bestE   device double [B]: energy of bestX re-scored in float64
+ *   opts    NULL = tuned mode, fresh start
+ * Integer instances follow the oracle's trajectories bit for bit.
+ * Errors: HOBO_ERR_ARG, HOBO_ERR_OOM, HOBO_ERR_CUDA.
+ */
+int hobo_anneal(hobo_h h, uint64_t seed, int B, const float* beta, int sweeps,
+                uint32_t* bestX, double* bestE, const hobo_anneal_opts* opts, void* stream);
+
+/* Human-readable message of the last error on this thread ("" if none). */
+const char* hobo_last_error(void);
+
+/* Library version string. */
+const char* hobo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOBO_H */

@@ -1,0 +1,227 @@
+"""Thin Python binding of the libhobo C ABI (include/hobo.h).
+
+Argument marshalling only: every step of the energy contraction and of the
+annealer runs in the library's CUDA kernels.  PyTorch supplies device
+memory and the current CUDA stream.  If the compiled library is missing the
+binding raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhobo.so")
+
+HOBO_OK = 0
+HOBO_ERR_ARG = -1
+HOBO_ERR_ORDER = -2
+HOBO_ERR_NOT_EXACT = -3
+HOBO_ERR_OOM = -4
+HOBO_ERR_CUDA = -5
+HOBO_ERR_TIMEOUT = -6
+HOBO_ERR_UNSUPPORTED = -7
+
+HOBO_INTEGER = 1
+HOBO_FORCE_SPARSE = 2
+HOBO_FORCE_DENSE = 4
+HOBO_SPLIT3 = 8
+
+HOBO_ANNEAL_TUNED = 0
+HOBO_ANNEAL_PLAIN = 1
+
+PATH_AUTO, PATH_TERMS, PATH_TENSOR_CORE = 0, 1, 2
+
+HOBO_MAX_ORDER = 8
+
+
+class HoboError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hobo error {code}: {msg}")
+        self.code = code
+
+
+class hobo_info_t(C.Structure):
+    _fields_ = [("N", C.c_int), ("order", C.c_int), ("words", C.c_int), ("dense", C.c_int),
+                ("integer", C.c_int), ("terms", C.c_int64 * (HOBO_MAX_ORDER + 1)),
+                ("abs_sum", C.c_double)]
+
+
+class hobo_anneal_opts(C.Structure):
+    _fields_ = [("mode", C.c_int), ("states_per_block", C.c_int), ("sweep0", C.c_int),
+                ("resume", C.c_int), ("X_io", C.c_void_p), ("bestE32_io", C.c_void_p),
+                ("E_io", C.c_void_p), ("g_io", C.c_void_p), ("accepts", C.c_void_p), ("ev_sweep_begin", C.c_void_p),
+                ("ev_sweep_end", C.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load libhobo.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libhobo.so not built ({path}); run paper_2407_19987_gb300/build.py")
+    L = C.CDLL(path)
+    P, I, I64, U64 = C.c_void_p, C.c_int, C.c_int64, C.c_uint64
+    L.hobo_create.argtypes = [C.POINTER(P), P, I, I, C.c_uint]
+    L.hobo_create_terms.argtypes = [C.POINTER(P), P, P, I64, I, I, C.c_uint]
+    L.hobo_destroy.argtypes = [P]
+    L.hobo_destroy.restype = None
+    L.hobo_info.argtypes = [P, C.POINTER(hobo_info_t)]
+    L.hobo_energy.argtypes = [P, P, I, P, P, P]
+    L.hobo_energy_path.argtypes = [P, P, I, P, P, I, P]
+    L.hobo_energy_fp64.argtypes = [P, P, I, P, P]
+    L.hobo_anneal.argtypes = [P, U64, I, P, I, P, P, C.POINTER(hobo_anneal_opts), P]
+    L.hobo_last_error.restype = C.c_char_p
+    L.hobo_version.restype = C.c_char_p
+    for name in ("hobo_create", "hobo_create_terms", "hobo_info", "hobo_energy", "hobo_energy_path",
+                 "hobo_energy_fp64", "hobo_anneal"):
+        getattr(L, name).restype = I
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != HOBO_OK:
+        raise HoboError(rc, load_library().hobo_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def words(N: int) -> int:
+    return (N + 31) // 32
+
+
+class Instance:
+    """A HOBO instance resident on the current CUDA device (hobo_create)."""
+
+    def __init__(self, handle: int, N: int, order: int):
+        self._h = C.c_void_p(handle)
+        self.N = N
+        self.order = order
+        self.W = words(N)
+
+    @classmethod
+    def from_dense(cls, T: np.ndarray, flags: int = 0) -> "Instance":
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        order, N = T.ndim, T.shape[0]
+        if any(s != N for s in T.shape):
+            raise ValueError("dense tensor must have shape (N,)*order")
+        h = C.c_void_p()
+        _check(load_library().hobo_create(C.byref(h), T.ctypes.data_as(C.c_void_p), order, N, flags))
+        return cls(h.value, N, order)
+
+    @classmethod
+    def from_terms(cls, idx: np.ndarray, coef: np.ndarray, N: int, flags: int = 0) -> "Instance":
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        coef = np.ascontiguousarray(coef, dtype=np.float32)
+        nnz, order = idx.shape
+        h = C.c_void_p()
+        _check(load_library().hobo_create_terms(C.byref(h), idx.ctypes.data_as(C.c_void_p),
+                                                coef.ctypes.data_as(C.c_void_p), nnz, order, N, flags))
+        return cls(h.value, N, order)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load_library().hobo_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> C.c_void_p:
+        return self._h
+
+    def info(self) -> dict:
+        inf = hobo_info_t()
+        _check(load_library().hobo_info(self._h, C.byref(inf)))
+        return dict(N=inf.N, order=inf.order, words=inf.words, dense=bool(inf.dense),
+                    integer=bool(inf.integer), terms=list(inf.terms), abs_sum=inf.abs_sum)
+
+    def energy(self, X, with_delta: bool = True, path: int = PATH_AUTO, stream=None):
+        """X: int32 CUDA tensor [B, W] of packed states.  Returns (E [B] f32,
+        dE [B, N] f32 or None)."""
+        import torch
+        B = X.shape[0]
+        E = torch.empty(B, dtype=torch.float32, device=X.device)
+        dE = torch.empty((B, self.N), dtype=torch.float32, device=X.device) if with_delta else None
+        _check(load_library().hobo_energy_path(self._h, _ptr(X), B, _ptr(E), _ptr(dE), path,
+                                               _stream(stream)))
+        return E, dE
+
+    def energy_into(self, X, E, dE=None, path: int = PATH_AUTO, stream=None):
+        _check(load_library().hobo_energy_path(self._h, _ptr(X), X.shape[0], _ptr(E), _ptr(dE), path,
+                                               _stream(stream)))
+
+    def energy_fp64(self, X, stream=None):
+        import torch
+        B = X.shape[0]
+        E = torch.empty(B, dtype=torch.float64, device=X.device)
+        _check(load_library().hobo_energy_fp64(self._h, _ptr(X), B, _ptr(E), _stream(stream)))
+        return E
+
+    def anneal(self, seed: int, B: int, betas: np.ndarray, *, mode: int = HOBO_ANNEAL_TUNED,
+               states_per_block: int = 0, sweep0: int = 0, resume: bool = False, X=None,
+               bestX=None, bestE32=None, E=None, g=None, want_final: bool = False,
+               want_fields: bool = False, want_accepts: bool = False, device=None, stream=None,
+               sweep_events=None) -> dict:
+        """Batched annealing (hobo_anneal).  betas: host float32 [sweeps].
+        Returns a dict of CUDA tensors: bestX [B, W] int32, bestE [B] f64, and
+        when asked X (final), E (final f32), bestE32, accepts."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        betas = np.ascontiguousarray(betas, dtype=np.float32)
+        if bestX is None:
+            bestX = torch.zeros((B, self.W), dtype=torch.int32, device=dev)
+        bestE = torch.empty(B, dtype=torch.float64, device=dev)
+        if X is None and (want_final or resume):
+            X = torch.zeros((B, self.W), dtype=torch.int32, device=dev)
+        if bestE32 is None:
+            bestE32 = torch.empty(B, dtype=torch.float32, device=dev)
+        if E is None and (want_final or want_fields):
+            E = torch.empty(B, dtype=torch.float32, device=dev)
+        if g is None and want_fields:
+            g = torch.empty((B, self.N), dtype=torch.float32, device=dev)
+        acc = torch.zeros(B, dtype=torch.int64, device=dev) if want_accepts else None
+        ev0 = ev1 = None
+        if sweep_events is not None:
+            for e in sweep_events:          # torch creates its events lazily
+                if not e.cuda_event:
+                    e.record()
+            ev0, ev1 = sweep_events[0].cuda_event, sweep_events[1].cuda_event
+        o = hobo_anneal_opts(mode, states_per_block, sweep0, 1 if resume else 0,
+                             _ptr(X), _ptr(bestE32), _ptr(E), _ptr(g), _ptr(acc), ev0, ev1)
+        _check(load_library().hobo_anneal(self._h, C.c_uint64(seed & (2 ** 64 - 1)), B,
+                                          betas.ctypes.data_as(C.c_void_p), betas.shape[0],
+                                          _ptr(bestX), _ptr(bestE), C.byref(o), _stream(stream)))
+        out = dict(bestX=bestX, bestE=bestE, bestE32=bestE32)
+        if X is not None:
+            out["X"] = X
+        if E is not None:
+            out["E"] = E
+        if g is not None:
+            out["g"] = g
+        if acc is not None:
+            out["accepts"] = acc
+        return out
+
+
+def version() -> str:
+    return load_library().hobo_version().decode()

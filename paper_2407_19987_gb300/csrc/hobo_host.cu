@@ -1,0 +1,562 @@
+// Host side of the C ABI: argument validation, canonicalisation of the HOBO
+// tensor into folded monomials, construction of the device layouts, and the
+// launch sequences of hobo_energy / hobo_anneal.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include "hobo_internal.h"
+
+namespace hobo {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+static int fail(int code, const std::string& msg)
+{
+    set_error(msg);
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(HOBO_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define HOBO_CUDA(call)                                                  \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);              \
+    } while (0)
+
+// A folded monomial: its distinct variables (ascending) and coefficient.
+struct Mono {
+    uint16_t v[HOBO_MAX_ORDER];
+    uint8_t d;
+};
+
+static bool mono_less(const Mono& a, const Mono& b)
+{
+    if (a.d != b.d) return a.d < b.d;
+    for (int q = 0; q < a.d; ++q)
+        if (a.v[q] != b.v[q]) return a.v[q] < b.v[q];
+    return false;
+}
+
+static bool mono_eq(const Mono& a, const Mono& b)
+{
+    if (a.d != b.d) return false;
+    for (int q = 0; q < a.d; ++q)
+        if (a.v[q] != b.v[q]) return false;
+    return true;
+}
+
+struct Entry {
+    Mono m;
+    double c;
+};
+
+// Fold one tensor entry: sort its indices and drop repeats (x*x = x).
+static bool fold_entry(const int64_t* tup, int order, int N, Mono& m)
+{
+    int64_t s[HOBO_MAX_ORDER];
+    for (int q = 0; q < order; ++q) {
+        if (tup[q] < 0 || tup[q] >= N) return false;
+        s[q] = tup[q];
+    }
+    std::sort(s, s + order);
+    int d = 0;
+    for (int q = 0; q < order; ++q)
+        if (q == 0 || s[q] != s[q - 1]) m.v[d++] = (uint16_t)s[q];
+    for (int q = d; q < HOBO_MAX_ORDER; ++q) m.v[q] = 0;
+    m.d = (uint8_t)d;
+    return true;
+}
+
+template <typename T>
+static int upload(T** dst, const std::vector<T>& src)
+{
+    *dst = nullptr;
+    if (src.empty()) return HOBO_OK;
+    cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * src.size());
+    if (e != cudaSuccess) return fail(HOBO_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    return HOBO_OK;
+}
+
+static void free_layouts(DevLayouts& d)
+{
+    void* ptrs[] = {d.tvars, d.tcoef32, d.tcoef64, d.fptr, d.fvars, d.fcoef, d.bptr, d.rtgt,
+                    d.rbeg, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3bf[0], d.S3bf[1], d.S3bf[2]};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    d = DevLayouts{};
+}
+
+static uint16_t bf16_bits_rn(float f)
+{
+    __nv_bfloat16 b = __float2bfloat16_rn(f);
+    uint16_t u;
+    std::memcpy(&u, &b, 2);
+    return u;
+}
+
+static float bf16_value(uint16_t u)
+{
+    uint32_t w = (uint32_t)u << 16;
+    float f;
+    std::memcpy(&f, &w, 4);
+    return f;
+}
+
+static double choose_split(double c, int nsplit, uint16_t out[3])
+{
+    double r = c;
+    for (int q = 0; q < nsplit; ++q) {
+        out[q] = bf16_bits_rn((float)r);
+        r -= (double)bf16_value(out[q]);
+    }
+    return r;   // residual not represented
+}
+
+// Build every layout from the folded monomial list (sorted by degree, then
+// variables) and upload it.
+static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned flags)
+{
+    const int N = h->N, K = h->order;
+    h->KF = std::max(K - 1, 1);
+    // condition slots per update entry: the sweep kernels are compiled for
+    // 1, 2 or 6 slots, so the layout stride is rounded up to one of those
+    h->KU = K <= 3 ? 1 : (K == 4 ? 2 : 6);
+    h->W = (N + 31) / 32;
+
+    double abs_sum = 0.0, maxabs = 0.0;
+    bool all_int = true;
+    for (auto& e : mono) {
+        h->terms[e.m.d]++;
+        abs_sum += std::fabs(e.c);
+        maxabs = std::max(maxabs, std::fabs(e.c));
+        if (e.c != std::nearbyint(e.c)) all_int = false;
+    }
+    h->abs_sum = abs_sum;
+    h->integer = all_int && abs_sum < 16777216.0;
+    if ((flags & HOBO_INTEGER) && !h->integer)
+        return fail(HOBO_ERR_NOT_EXACT, all_int ? "sum of |coefficients| >= 2^24"
+                                                : "non-integer coefficient with HOBO_INTEGER");
+
+    const int64_t M = (int64_t)mono.size();
+    DevLayouts& d = h->d;
+    d.M = M;
+
+    // (1) monomial list
+    {
+        std::vector<uint16_t> tv((size_t)M * K);
+        std::vector<float> c32((size_t)M);
+        std::vector<double> c64((size_t)M);
+        for (int64_t t = 0; t < M; ++t) {
+            for (int q = 0; q < K; ++q)
+                tv[(size_t)t * K + q] = q < mono[t].m.d ? mono[t].m.v[q] : (uint16_t)N;
+            c32[t] = (float)mono[t].c;
+            c64[t] = mono[t].c;
+        }
+        int rc;
+        if ((rc = upload(&d.tvars, tv)) || (rc = upload(&d.tcoef32, c32)) || (rc = upload(&d.tcoef64, c64)))
+            return rc;
+    }
+    // (2) field list by variable
+    {
+        const int KF = h->KF;
+        std::vector<int64_t> ptr((size_t)N + 1, 0);
+        for (auto& e : mono)
+            for (int q = 0; q < e.m.d; ++q) ptr[e.m.v[q] + 1]++;
+        for (int j = 0; j < N; ++j) ptr[j + 1] += ptr[j];
+        d.F = ptr[N];
+        std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+        std::vector<uint16_t> fv((size_t)std::max<int64_t>(d.F, 1) * KF, (uint16_t)N);
+        std::vector<float> fc((size_t)std::max<int64_t>(d.F, 1), 0.0f);
+        for (auto& e : mono)
+            for (int q = 0; q < e.m.d; ++q) {
+                const int j = e.m.v[q];
+                const int64_t at = fill[j]++;
+                int s = 0;
+                for (int r = 0; r < e.m.d; ++r)
+                    if (r != q) fv[(size_t)at * KF + s++] = e.m.v[r];
+                fc[at] = (float)e.c;
+            }
+        int rc;
+        if ((rc = upload(&d.fptr, ptr)) || (rc = upload(&d.fvars, fv)) || (rc = upload(&d.fcoef, fc)))
+            return rc;
+    }
+
+    // dense layout decision: order 3, N <= 512, cubic part at least 25% full
+    const double c3 = (double)N * (N - 1) * (N - 2) / 6.0;
+    bool dense = false;
+    if (K == 3 && N <= 512 && !(flags & HOBO_FORCE_SPARSE)) {
+        if ((flags & HOBO_FORCE_DENSE) || (c3 > 0 && (double)h->terms[3] >= 0.25 * c3)) dense = true;
+    }
+    h->dense = dense;
+
+    if (dense) {
+        const int P = (N + 3) & ~3;
+        std::vector<float> a((size_t)N, 0.0f), S2((size_t)N * P, 0.0f);
+        std::vector<float> S3((size_t)N * N * P, 0.0f);
+        for (auto& e : mono) {
+            const float c = (float)e.c;
+            if (e.m.d == 1) a[e.m.v[0]] = c;
+            else if (e.m.d == 2) {
+                const int i = e.m.v[0], j = e.m.v[1];
+                S2[(size_t)i * P + j] = c;
+                S2[(size_t)j * P + i] = c;
+            } else {
+                const int v[3] = {e.m.v[0], e.m.v[1], e.m.v[2]};
+                const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+                for (auto& pm : perm)
+                    S3[((size_t)v[pm[0]] * N + v[pm[1]]) * P + v[pm[2]]] = c;
+            }
+        }
+        int rc;
+        if ((rc = upload(&d.a, a)) || (rc = upload(&d.S2, S2)) || (rc = upload(&d.S3, S3))) return rc;
+
+        // bf16 split planes for the tensor-core contraction: [m][j][l] with
+        // K (= l) pitch KP = N rounded up to 64, rows m*N + j.
+        int nsplit = 2;
+        if ((flags & HOBO_SPLIT3) || (h->integer && maxabs >= 65536.0)) nsplit = 3;
+        d.nsplit = nsplit;
+        const int KP = (N + 63) & ~63;
+        std::vector<uint16_t> planes[3];
+        for (int q = 0; q < nsplit; ++q) planes[q].assign((size_t)N * N * KP, 0);
+        for (auto& e : mono) {
+            if (e.m.d != 3) continue;
+            uint16_t sp[3];
+            choose_split(e.c, nsplit, sp);
+            const int v[3] = {e.m.v[0], e.m.v[1], e.m.v[2]};
+            const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+            for (auto& pm : perm)
+                for (int q = 0; q < nsplit; ++q)
+                    planes[q][((size_t)v[pm[0]] * N + v[pm[1]]) * KP + v[pm[2]]] = sp[q];
+        }
+        for (int q = 0; q < nsplit; ++q)
+            if ((rc = upload(&d.S3bf[q], planes[q]))) return rc;
+    } else {
+        // (3) update lists grouped by (flipped bit i, target j)
+        const int KU = h->KU;
+        std::vector<int32_t> cnt((size_t)N * N, 0);
+        int64_t U = 0;
+        for (auto& e : mono) {
+            if (e.m.d < 2) continue;
+            for (int a = 0; a < e.m.d; ++a)
+                for (int b = 0; b < e.m.d; ++b)
+                    if (a != b) { cnt[(size_t)e.m.v[a] * N + e.m.v[b]]++; ++U; }
+        }
+        if (U >= (int64_t)INT32_MAX) return fail(HOBO_ERR_UNSUPPORTED, "update list too large");
+        std::vector<int32_t> bptr((size_t)N + 1, 0), rtgt, rbeg;
+        std::vector<int32_t> cell_rec((size_t)N * N, -1);
+        int32_t acc = 0;
+        for (int i = 0; i < N; ++i) {
+            bptr[i] = (int32_t)rtgt.size();
+            for (int j = 0; j < N; ++j) {
+                const int32_t c = cnt[(size_t)i * N + j];
+                if (!c) continue;
+                cell_rec[(size_t)i * N + j] = (int32_t)rtgt.size();
+                rtgt.push_back(j);
+                rbeg.push_back(acc);
+                acc += c;
+            }
+        }
+        bptr[N] = (int32_t)rtgt.size();
+        rbeg.push_back(acc);
+        std::vector<int32_t> fill(rbeg.begin(), rbeg.end() - 1);
+        std::vector<float> uc((size_t)std::max<int64_t>(U, 1), 0.0f);
+        std::vector<uint16_t> ucond((size_t)std::max<int64_t>(U, 1) * KU, (uint16_t)N);
+        for (auto& e : mono) {
+            if (e.m.d < 2) continue;
+            for (int a = 0; a < e.m.d; ++a)
+                for (int b = 0; b < e.m.d; ++b) {
+                    if (a == b) continue;
+                    const int32_t rec = cell_rec[(size_t)e.m.v[a] * N + e.m.v[b]];
+                    const int32_t at = fill[rec]++;
+                    uc[at] = (float)e.c;
+                    int s = 0;
+                    for (int r = 0; r < e.m.d; ++r)
+                        if (r != a && r != b) ucond[(size_t)at * KU + s++] = e.m.v[r];
+                }
+        }
+        d.R = (int64_t)rtgt.size();
+        d.U = U;
+        if (rtgt.empty()) rtgt.push_back(0);
+        int rc;
+        if ((rc = upload(&d.bptr, bptr)) || (rc = upload(&d.rtgt, rtgt)) || (rc = upload(&d.rbeg, rbeg)) ||
+            (rc = upload(&d.ucoef, uc)) || (rc = upload(&d.uconds, ucond)))
+            return rc;
+    }
+    return HOBO_OK;
+}
+
+static int create_from_entries(hobo_h* out, std::vector<Entry>& ent, int order, int N, unsigned flags)
+{
+    std::stable_sort(ent.begin(), ent.end(), [](const Entry& a, const Entry& b) { return mono_less(a.m, b.m); });
+    std::vector<Entry> mono;
+    mono.reserve(ent.size());
+    for (size_t q = 0; q < ent.size();) {
+        size_t r = q;
+        double c = 0.0;
+        while (r < ent.size() && mono_eq(ent[r].m, ent[q].m)) c += ent[r++].c;
+        if (c != 0.0) mono.push_back({ent[q].m, c});
+        q = r;
+    }
+    ent.clear();
+    ent.shrink_to_fit();
+
+    if (flags & HOBO_INTEGER) {
+        double abs_sum = 0.0;
+        bool all_int = true;
+        for (auto& e : mono) {
+            abs_sum += std::fabs(e.c);
+            if (e.c != std::nearbyint(e.c)) all_int = false;
+        }
+        if (!all_int) return fail(HOBO_ERR_NOT_EXACT, "non-integer coefficient with HOBO_INTEGER");
+        if (!(abs_sum < 16777216.0)) return fail(HOBO_ERR_NOT_EXACT, "sum of |coefficients| >= 2^24");
+    }
+    hobo_instance* h = new (std::nothrow) hobo_instance();
+    if (!h) return fail(HOBO_ERR_OOM, "host allocation failed");
+    h->N = N;
+    h->order = order;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+    const int rc = build_instance(h, mono, flags);
+    if (rc != HOBO_OK) {
+        const std::string msg = g_err;
+        free_layouts(h->d);
+        delete h;
+        set_error(msg);
+        return rc;
+    }
+    *out = h;
+    set_error("");
+    return HOBO_OK;
+}
+
+static int check_shape(int order, int N)
+{
+    if (order < 1 || order > HOBO_MAX_ORDER) return fail(HOBO_ERR_ORDER, "order must be 1..8");
+    if (N < 1 || N > HOBO_MAX_N) return fail(HOBO_ERR_ARG, "N must be 1..1024");
+    return HOBO_OK;
+}
+
+}  // namespace hobo
+
+using namespace hobo;
+
+extern "C" {
+
+int hobo_create(hobo_h* out, const float* T, int order, int N, unsigned flags)
+{
+    if (!out) return fail(HOBO_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!T) return fail(HOBO_ERR_ARG, "T is NULL");
+    int rc = check_shape(order, N);
+    if (rc) return rc;
+    double total = std::pow((double)N, (double)order);
+    if (total > 9.0e15) return fail(HOBO_ERR_ARG, "N^order too large");
+    const int64_t n = (int64_t)total;
+    std::vector<Entry> ent;
+    int64_t tup[HOBO_MAX_ORDER] = {0};
+    for (int64_t f = 0; f < n; ++f) {
+        if (f > 0) {   // odometer over the index tuple, last index fastest
+            for (int q = order - 1; q >= 0; --q) {
+                if (++tup[q] < N) break;
+                tup[q] = 0;
+            }
+        }
+        const float v = T[f];
+        if (v == 0.0f) continue;
+        if (!std::isfinite(v)) return fail(HOBO_ERR_ARG, "non-finite tensor entry");
+        Entry e;
+        fold_entry(tup, order, N, e.m);
+        e.c = (double)v;
+        ent.push_back(e);
+    }
+    return create_from_entries(out, ent, order, N, flags);
+}
+
+int hobo_create_terms(hobo_h* out, const int32_t* idx, const float* coef, int64_t nnz, int order,
+                      int N, unsigned flags)
+{
+    if (!out) return fail(HOBO_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_shape(order, N);
+    if (rc) return rc;
+    if (nnz < 0 || (nnz > 0 && (!idx || !coef))) return fail(HOBO_ERR_ARG, "bad term arrays");
+    std::vector<Entry> ent;
+    ent.reserve((size_t)nnz);
+    int64_t tup[HOBO_MAX_ORDER];
+    for (int64_t t = 0; t < nnz; ++t) {
+        for (int q = 0; q < order; ++q) tup[q] = idx[t * order + q];
+        const float v = coef[t];
+        if (!std::isfinite(v)) return fail(HOBO_ERR_ARG, "non-finite coefficient");
+        if (v == 0.0f) continue;
+        Entry e;
+        if (!fold_entry(tup, order, N, e.m))
+            return fail(HOBO_ERR_ARG, "index out of range in term " + std::to_string(t));
+        e.c = (double)v;
+        ent.push_back(e);
+    }
+    return create_from_entries(out, ent, order, N, flags);
+}
+
+void hobo_destroy(hobo_h h)
+{
+    if (!h) return;
+    free_layouts(h->d);
+    delete h;
+}
+
+int hobo_info(hobo_h h, hobo_info_t* info)
+{
+    if (!h || !info) return fail(HOBO_ERR_ARG, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->N = h->N;
+    info->order = h->order;
+    info->words = h->W;
+    info->dense = h->dense ? 1 : 0;
+    info->integer = h->integer ? 1 : 0;
+    for (int q = 0; q <= HOBO_MAX_ORDER; ++q) info->terms[q] = h->terms[q];
+    info->abs_sum = h->abs_sum;
+    return HOBO_OK;
+}
+
+static int energy_impl(hobo_h h, const uint32_t* X, int B, float* E, float* g, bool flip, int path,
+                       cudaStream_t st)
+{
+    if (path == 2 || (path == 0 && h->dense)) {
+        cudaError_t e = launch_energy_tc(h, X, B, E, g, flip, st);
+        if (e == cudaSuccess) return HOBO_OK;
+        if (e != cudaErrorNotSupported) return cuda_fail(e, "tensor-core contraction");
+        if (path == 2) return fail(HOBO_ERR_UNSUPPORTED, "tensor-core path needs a dense order-3 instance");
+        (void)cudaGetLastError();
+    }
+    cudaError_t e = launch_energy_terms(h, X, B, E, g, flip, st);
+    if (e != cudaSuccess) return cuda_fail(e, "term-list contraction");
+    return HOBO_OK;
+}
+
+int hobo_energy_path(hobo_h h, const uint32_t* X, int B, float* E, float* dE, int path, void* stream)
+{
+    if (!h) return fail(HOBO_ERR_ARG, "NULL instance");
+    if (B < 0 || (B > 0 && (!X || !E))) return fail(HOBO_ERR_ARG, "bad X/E/B");
+    if (path < 0 || path > 2) return fail(HOBO_ERR_ARG, "path must be 0, 1 or 2");
+    if (B == 0) return HOBO_OK;
+    return energy_impl(h, X, B, E, dE, true, path, (cudaStream_t)stream);
+}
+
+int hobo_energy(hobo_h h, const uint32_t* X, int B, float* E, float* dE, void* stream)
+{
+    return hobo_energy_path(h, X, B, E, dE, 0, stream);
+}
+
+int hobo_energy_fp64(hobo_h h, const uint32_t* X, int B, double* E, void* stream)
+{
+    if (!h) return fail(HOBO_ERR_ARG, "NULL instance");
+    if (B < 0 || (B > 0 && (!X || !E))) return fail(HOBO_ERR_ARG, "bad X/E/B");
+    if (B == 0) return HOBO_OK;
+    cudaError_t e = launch_energy_fp64(h, X, B, E, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fp64 energy");
+    return HOBO_OK;
+}
+
+int hobo_anneal(hobo_h h, uint64_t seed, int B, const float* beta, int sweeps, uint32_t* bestX,
+                double* bestE, const hobo_anneal_opts* opts, void* stream)
+{
+    if (!h) return fail(HOBO_ERR_ARG, "NULL instance");
+    if (B < 0 || sweeps < 0) return fail(HOBO_ERR_ARG, "negative B or sweeps");
+    if (B == 0) return HOBO_OK;
+    if (!bestX || !bestE) return fail(HOBO_ERR_ARG, "NULL bestX/bestE");
+    if (sweeps > 0 && !beta) return fail(HOBO_ERR_ARG, "NULL beta");
+    hobo_anneal_opts o{};
+    if (opts) o = *opts;
+    if (o.mode != HOBO_ANNEAL_TUNED && o.mode != HOBO_ANNEAL_PLAIN) return fail(HOBO_ERR_ARG, "bad mode");
+    if (o.resume && (!o.X_io || !o.bestE32_io)) return fail(HOBO_ERR_ARG, "resume needs X_io and bestE32_io");
+    if (o.sweep0 < 0) return fail(HOBO_ERR_ARG, "negative sweep0");
+    for (int s = 0; s < sweeps; ++s)
+        if (!(beta[s] >= 0.0f) || !std::isfinite(beta[s])) return fail(HOBO_ERR_ARG, "beta must be finite and >= 0");
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = h->N, W = h->W;
+    float* d_beta = nullptr;
+    uint32_t* d_X = o.X_io;
+    float* d_g = nullptr;
+    float* d_E = nullptr;
+    float* d_bE = o.bestE32_io;
+    bool own_X = false, own_bE = false;
+    int rc = HOBO_OK;
+    auto cleanup = [&]() {
+        if (d_beta) cudaFreeAsync(d_beta, st);
+        if (own_X && d_X) cudaFreeAsync(d_X, st);
+        if (d_g && d_g != o.g_io) cudaFreeAsync(d_g, st);
+        if (d_E && d_E != o.E_io) cudaFreeAsync(d_E, st);
+        if (own_bE && d_bE) cudaFreeAsync(d_bE, st);
+    };
+#define ACHECK(call, what)                                            \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) { rc = cuda_fail(e_, what); cleanup(); return rc; } \
+    } while (0)
+
+    if (sweeps > 0) {
+        ACHECK(cudaMallocAsync((void**)&d_beta, sizeof(float) * sweeps, st), "cudaMallocAsync beta");
+        ACHECK(cudaMemcpyAsync(d_beta, beta, sizeof(float) * sweeps, cudaMemcpyHostToDevice, st), "beta copy");
+    }
+    if (!d_X) {
+        ACHECK(cudaMallocAsync((void**)&d_X, sizeof(uint32_t) * (size_t)B * W, st), "cudaMallocAsync X");
+        own_X = true;
+    }
+    if (!d_bE) {
+        ACHECK(cudaMallocAsync((void**)&d_bE, sizeof(float) * (size_t)B, st), "cudaMallocAsync bestE");
+        own_bE = true;
+    }
+    if (o.g_io) d_g = o.g_io;
+    else ACHECK(cudaMallocAsync((void**)&d_g, sizeof(float) * (size_t)B * N, st), "cudaMallocAsync g");
+    if (o.E_io) d_E = o.E_io;
+    else ACHECK(cudaMallocAsync((void**)&d_E, sizeof(float) * (size_t)B, st), "cudaMallocAsync E");
+
+    if (!o.resume) ACHECK(launch_init_states(d_X, B, N, W, seed, st), "init states");
+    if (!(o.resume && o.g_io && o.E_io)) {
+        rc = energy_impl(h, d_X, B, d_E, d_g, false, 0, st);
+        if (rc != HOBO_OK) { cleanup(); return rc; }
+    }
+
+    SweepArgs a;
+    a.B = B; a.sweeps = sweeps; a.sweep0 = o.sweep0; a.resume = o.resume; a.seed = seed;
+    a.S = o.states_per_block;
+    a.beta = d_beta; a.X = d_X; a.g = d_g; a.E = d_E; a.bestX = bestX; a.bestE = d_bE;
+    a.accepts = o.accepts;
+    a.write_g = o.g_io != nullptr;
+    if (sweeps > 0) {
+        if (o.ev_sweep_begin) ACHECK(cudaEventRecord((cudaEvent_t)o.ev_sweep_begin, st), "event record");
+        if (o.mode == HOBO_ANNEAL_PLAIN) ACHECK(launch_sweep_plain(h, a, st), "plain sweep");
+        else ACHECK(launch_sweep_tuned(h, a, st), "tuned sweep");
+        if (o.ev_sweep_end) ACHECK(cudaEventRecord((cudaEvent_t)o.ev_sweep_end, st), "event record");
+    } else if (!o.resume) {
+        ACHECK(cudaMemcpyAsync(bestX, d_X, sizeof(uint32_t) * (size_t)B * W, cudaMemcpyDeviceToDevice, st), "bestX");
+        ACHECK(cudaMemcpyAsync(d_bE, d_E, sizeof(float) * (size_t)B, cudaMemcpyDeviceToDevice, st), "bestE");
+    }
+    ACHECK(launch_energy_fp64(h, bestX, B, bestE, st), "fp64 re-score");
+    cleanup();
+    set_error("");
+    return HOBO_OK;
+#undef ACHECK
+}
+
+const char* hobo_last_error(void) { return g_err.c_str(); }
+
+const char* hobo_version(void) { return "hobo-gb300 0.1"; }
+
+}  // extern "C"

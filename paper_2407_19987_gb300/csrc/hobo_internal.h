@@ -1,0 +1,97 @@
+// Internal declarations shared by the host library and the kernel files.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <cuda_runtime.h>
+#include "hobo.h"
+
+namespace hobo {
+
+// Device copies of one instance's layouts.  All arrays are owned by the
+// instance and freed by hobo_destroy.
+struct DevLayouts {
+    // (1) folded monomial list, all degrees, `K = order` variable slots per
+    //     monomial padded with the sentinel index N (whose bit reads as 1).
+    int64_t M = 0;
+    uint16_t* tvars = nullptr;   // [M][K]
+    float* tcoef32 = nullptr;    // [M]
+    double* tcoef64 = nullptr;   // [M]
+
+    // (2) field list by variable: entry e of variable j holds the
+    //     coefficient of a monomial containing j and its other members
+    //     (KF = max(order-1,1) slots, sentinel N).
+    int64_t F = 0;
+    int64_t* fptr = nullptr;     // [N+1]
+    uint16_t* fvars = nullptr;   // [F][KF]
+    float* fcoef = nullptr;      // [F]
+
+    // (3) update list by flipped bit (sparse sweep): for bit i, target
+    //     records bptr[i]..bptr[i+1]; record r updates field rtgt[r] with
+    //     the entries rbeg[r]..rbeg[r+1], each a coefficient and the other
+    //     members of the monomial besides i and the target (KU slots).
+    int64_t R = 0, U = 0;
+    int32_t* bptr = nullptr;     // [N+1]
+    int32_t* rtgt = nullptr;     // [R]
+    int32_t* rbeg = nullptr;     // [R+1]
+    float* ucoef = nullptr;      // [U]
+    uint16_t* uconds = nullptr;  // [U][KU]
+
+    // (4) dense order<=3 layout: linear a[N], symmetric pair matrix S2[N][N]
+    //     and symmetric cubic tensor S3[N][N][N] (zero where indices repeat),
+    //     float32; bf16 split planes of S3 for the tensor-core contraction.
+    float* a = nullptr;
+    float* S2 = nullptr;
+    float* S3 = nullptr;
+    uint16_t* S3bf[3] = {nullptr, nullptr, nullptr};
+    int nsplit = 0;
+};
+
+}  // namespace hobo
+
+struct hobo_instance {
+    int N = 0, order = 0, W = 0;
+    int KF = 1, KU = 1;
+    bool dense = false, integer = false;
+    int64_t terms[HOBO_MAX_ORDER + 1] = {0};
+    double abs_sum = 0.0;
+    int device = 0;
+    int num_sms = 0;
+    hobo::DevLayouts d;
+};
+
+namespace hobo {
+
+// ---- kernel launchers (hobo_kernels.cu / hobo_tc.cu) ---------------------
+cudaError_t launch_init_states(uint32_t* X, int B, int N, int W, uint64_t seed, cudaStream_t st);
+
+// g_or_dE: [B][N] or null; flip_out: write (1-2x)g instead of g
+cudaError_t launch_energy_terms(const hobo_instance* h, const uint32_t* X, int B, float* E,
+                                float* g_or_dE, bool flip_out, cudaStream_t st);
+
+cudaError_t launch_energy_fp64(const hobo_instance* h, const uint32_t* X, int B, double* E,
+                               cudaStream_t st);
+
+struct SweepArgs {
+    int B = 0, sweeps = 0, sweep0 = 0, resume = 0, S = 32;
+    uint64_t seed = 0;
+    const float* beta = nullptr;   // device [sweeps]
+    uint32_t* X = nullptr;         // device [B][W] in: start states, out: final
+    float* g = nullptr;            // device [B][N] in: fields of X (plain: in/out)
+    float* E = nullptr;            // device [B] in: energies of X, out: final
+    uint32_t* bestX = nullptr;     // device [B][W]
+    float* bestE = nullptr;        // device [B]
+    int64_t* accepts = nullptr;    // device [B] or null
+    bool write_g = false;          // tuned: write the final fields back to g
+};
+
+cudaError_t launch_sweep_tuned(const hobo_instance* h, const SweepArgs& a, cudaStream_t st);
+cudaError_t launch_sweep_plain(const hobo_instance* h, const SweepArgs& a, cudaStream_t st);
+
+// tcgen05 dense order-3 contraction; returns cudaErrorNotSupported when the
+// instance has no dense layout.
+cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, float* E,
+                             float* g_or_dE, bool flip_out, cudaStream_t st);
+
+void set_error(const std::string& msg);
+
+}  // namespace hobo

@@ -1,0 +1,331 @@
+// CUDA-core kernels: random initial states, term-list energy/field
+// contraction (float32), float64 re-scoring, and the Metropolis sweeps
+// (tuned warp-per-state kernel and the plain thread-per-state kernel).
+#include <algorithm>
+#include "hobo_internal.h"
+#include "hobo_dev.cuh"
+#include "sweep_impl.cuh"
+
+namespace hobo {
+
+// ===========================================================================
+// Initial states: bit i of state b is bit 31 of word (i % 4) of
+// Philox(counter = (i/4, 0, b, 1), key = seed).
+// ===========================================================================
+__global__ void init_states_kernel(uint32_t* __restrict__ X, int B, int N, int W,
+                                   uint32_t k0, uint32_t k1)
+{
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (int64_t)B * W) return;
+    const int b = (int)(tid / W), w = (int)(tid % W);
+    uint32_t word = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const u32x4 r = philox10((uint32_t)(8 * w + q), 0u, (uint32_t)b, kStreamInit, k0, k1);
+        word |= ((r.a >> 31) << (4 * q)) | ((r.b >> 31) << (4 * q + 1)) |
+                ((r.c >> 31) << (4 * q + 2)) | ((r.d >> 31) << (4 * q + 3));
+    }
+    const int rem = N - 32 * w;
+    if (rem < 32) word &= (1u << rem) - 1u;
+    X[tid] = word;
+}
+
+cudaError_t launch_init_states(uint32_t* X, int B, int N, int W, uint64_t seed, cudaStream_t st)
+{
+    if (B == 0) return cudaSuccess;
+    const int64_t n = (int64_t)B * W;
+    const int threads = 256;
+    init_states_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
+        X, B, N, W, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Term-list contraction on CUDA cores.  A block holds 32 states (one per
+// lane) with their bits transposed in shared memory (word w of state b at
+// [w][b], plus the sentinel bit N that reads as 1).  Warps split the
+// variables: for variable j the field is the sum of the coefficients of the
+// monomials containing j whose other members are all set.  The energy is
+// the sum over monomials whose members are all set.
+// ===========================================================================
+constexpr int kTermThreads = 256;
+
+// Compensated summation (Kahan): acc + comp tracks the exact running sum to
+// within a few units in the last place, whatever the number of terms.
+__device__ __forceinline__ void kahan_add(float& acc, float& comp, float v)
+{
+    const float y = __fsub_rn(v, comp);
+    const float t = __fadd_rn(acc, y);
+    comp = __fsub_rn(__fsub_rn(t, acc), y);
+    acc = t;
+}
+
+template <bool FLIP>
+__global__ void __launch_bounds__(kTermThreads)
+energy_terms_kernel(const uint32_t* __restrict__ X, int B, int N, int W,
+                    const int64_t* __restrict__ fptr, const uint16_t* __restrict__ fvars,
+                    const float* __restrict__ fcoef, int KF,
+                    const uint16_t* __restrict__ tvars, const float* __restrict__ tcoef,
+                    int64_t M, int K, float* __restrict__ out_g, float* __restrict__ out_E)
+{
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int b0 = blockIdx.x * 32;
+    const int nb = min(32, B - b0);
+    const int WS = W + 1;
+    uint32_t* bits = smem;                              // [WS][32]
+    float* red = reinterpret_cast<float*>(bits + WS * 32);   // [nwarps][32]
+    float* gs = red + nwarps * 32;                      // [32][N+1]
+    const int NP = N + 1;
+
+    for (int q = threadIdx.x; q < WS * 32; q += blockDim.x) {
+        const int w = q >> 5, b = q & 31;
+        uint32_t v = 0;
+        if (w < W && b < nb) {
+            v = X[(int64_t)(b0 + b) * W + w];
+            const int rem = N - 32 * w;
+            if (rem < 32) v &= (1u << rem) - 1u;
+        }
+        if (w == (N >> 5)) v |= 1u << (N & 31);
+        bits[q] = v;
+    }
+    __syncthreads();
+
+    if (out_g) {
+        for (int j = warp; j < N; j += nwarps) {
+            float acc = 0.0f, comp = 0.0f;   // compensated (Kahan) sum
+            const int64_t e1 = fptr[j + 1];
+            for (int64_t e = fptr[j]; e < e1; ++e) {
+                const float c = fcoef[e];
+                uint32_t p = 1u;
+                for (int s = 0; s < KF; ++s) {
+                    const int v = fvars[e * KF + s];
+                    p &= bits[(v >> 5) * 32 + lane] >> (v & 31);
+                }
+                if (p & 1u) kahan_add(acc, comp, c);
+            }
+            if (FLIP && ((bits[(j >> 5) * 32 + lane] >> (j & 31)) & 1u)) acc = -acc;
+            gs[lane * NP + j] = acc;
+        }
+    }
+
+    float eacc = 0.0f, ecomp = 0.0f;
+    for (int64_t t = warp; t < M; t += nwarps) {
+        const float c = tcoef[t];
+        uint32_t p = 1u;
+        for (int s = 0; s < K; ++s) {
+            const int v = tvars[t * K + s];
+            p &= bits[(v >> 5) * 32 + lane] >> (v & 31);
+        }
+        if (p & 1u) kahan_add(eacc, ecomp, c);
+    }
+    red[warp * 32 + lane] = eacc;
+    __syncthreads();
+    if (warp == 0 && lane < nb) {
+        float e = 0.0f;
+        for (int q = 0; q < nwarps; ++q) e = __fadd_rn(e, red[q * 32 + lane]);
+        out_E[b0 + lane] = e;
+    }
+    if (out_g) {
+        for (int b = 0; b < nb; ++b)
+            for (int j = threadIdx.x; j < N; j += blockDim.x)
+                out_g[(int64_t)(b0 + b) * N + j] = gs[b * NP + j];
+    }
+}
+
+static size_t term_smem(int N, int W, bool with_g)
+{
+    return sizeof(uint32_t) * (size_t)(W + 1) * 32 + sizeof(float) * (kTermThreads / 32) * 32 +
+           (with_g ? sizeof(float) * 32 * (size_t)(N + 1) : 0);
+}
+
+cudaError_t launch_energy_terms(const hobo_instance* h, const uint32_t* X, int B, float* E,
+                                float* g_or_dE, bool flip_out, cudaStream_t st)
+{
+    if (B == 0) return cudaSuccess;
+    const size_t sm = term_smem(h->N, h->W, g_or_dE != nullptr);
+    const unsigned grid = (unsigned)((B + 31) / 32);
+    const auto& d = h->d;
+    if (flip_out) {
+        cudaFuncSetAttribute(energy_terms_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        energy_terms_kernel<true><<<grid, kTermThreads, sm, st>>>(
+            X, B, h->N, h->W, d.fptr, d.fvars, d.fcoef, h->KF, d.tvars, d.tcoef32, d.M, h->order,
+            g_or_dE, E);
+    } else {
+        cudaFuncSetAttribute(energy_terms_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        energy_terms_kernel<false><<<grid, kTermThreads, sm, st>>>(
+            X, B, h->N, h->W, d.fptr, d.fvars, d.fcoef, h->KF, d.tvars, d.tcoef32, d.M, h->order,
+            g_or_dE, E);
+    }
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// float64 re-scoring: same traversal as the energy part above, with the
+// folded coefficients kept in float64 and a float64 accumulator; the
+// per-warp partial sums are combined in a fixed order.
+// ===========================================================================
+__global__ void __launch_bounds__(kTermThreads)
+energy_fp64_kernel(const uint32_t* __restrict__ X, int B, int N, int W,
+                   const uint16_t* __restrict__ tvars, const double* __restrict__ tcoef,
+                   int64_t M, int K, double* __restrict__ out_E)
+{
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int b0 = blockIdx.x * 32;
+    const int nb = min(32, B - b0);
+    const int WS = W + 1;
+    uint32_t* bits = smem;
+    double* red = reinterpret_cast<double*>(bits + ((WS * 32 + 1) & ~1));
+    for (int q = threadIdx.x; q < WS * 32; q += blockDim.x) {
+        const int w = q >> 5, b = q & 31;
+        uint32_t v = 0;
+        if (w < W && b < nb) {
+            v = X[(int64_t)(b0 + b) * W + w];
+            const int rem = N - 32 * w;
+            if (rem < 32) v &= (1u << rem) - 1u;
+        }
+        if (w == (N >> 5)) v |= 1u << (N & 31);
+        bits[q] = v;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int64_t t = warp; t < M; t += nwarps) {
+        uint32_t p = 1u;
+        for (int s = 0; s < K; ++s) {
+            const int v = tvars[t * K + s];
+            p &= bits[(v >> 5) * 32 + lane] >> (v & 31);
+        }
+        if (p & 1u) acc += tcoef[t];
+    }
+    red[warp * 32 + lane] = acc;
+    __syncthreads();
+    if (warp == 0 && lane < nb) {
+        double e = 0.0;
+        for (int q = 0; q < nwarps; ++q) e += red[q * 32 + lane];
+        out_E[b0 + lane] = e;
+    }
+}
+
+cudaError_t launch_energy_fp64(const hobo_instance* h, const uint32_t* X, int B, double* E,
+                               cudaStream_t st)
+{
+    if (B == 0) return cudaSuccess;
+    const size_t sm = sizeof(uint32_t) * (((size_t)(h->W + 1) * 32 + 1) & ~(size_t)1) +
+                      sizeof(double) * (kTermThreads / 32) * 32;
+    energy_fp64_kernel<<<(unsigned)((B + 31) / 32), kTermThreads, sm, st>>>(
+        X, B, h->N, h->W, h->d.tvars, h->d.tcoef64, h->d.M, h->order, E);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Plain sweep: one thread per state, fields and bits in global memory.
+// ---------------------------------------------------------------------------
+template <bool DENSE, int KU>
+__global__ void sweep_plain_kernel(const SweepDev p)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.B) return;
+    const int N = p.N, W = p.W, P = p.P;
+    float* __restrict__ g = p.g + (int64_t)b * N;
+    uint32_t* __restrict__ x = p.X + (int64_t)b * W;
+    uint32_t* __restrict__ bx = p.bestX + (int64_t)b * W;
+    {
+        const int rem = N - 32 * (W - 1);
+        if (rem < 32) x[W - 1] &= (1u << rem) - 1u;
+    }
+    float E = p.E[b], Eb;
+    if (p.resume) {
+        Eb = p.bestE[b];
+    } else {
+        Eb = E;
+        for (int k = 0; k < W; ++k) bx[k] = x[k];
+    }
+    long long nacc = 0;
+    u32x4 r = {0u, 0u, 0u, 0u};
+    for (int s = 0; s < p.sweeps; ++s) {
+        const float beta = p.beta[s];
+        const uint32_t sw = (uint32_t)(p.sweep0 + s);
+        for (int i = 0; i < N; ++i) {
+            if ((i & 3) == 0)
+                r = philox10((uint32_t)(i >> 2), sw, (uint32_t)b, kStreamMetropolis, p.k0, p.k1);
+            const uint32_t xi = bit_of(x, i);
+            const float gi = g[i];
+            const float dE = xi ? -gi : gi;
+            if (!metropolis(dE, beta, pick4(r, i & 3))) continue;
+            x[i >> 5] ^= 1u << (i & 31);
+            E = __fadd_rn(E, dE);
+            ++nacc;
+            const float delta = xi ? -1.0f : 1.0f;
+            if (DENSE) {
+                const float* slab = p.S3 + (int64_t)i * N * P;
+                for (int j = 0; j < N; ++j) {
+                    float acc = 0.0f;
+                    for (int l = 0; l < N; ++l)
+                        if (bit_of(x, l)) acc = __fadd_rn(acc, slab[(int64_t)l * P + j]);
+                    g[j] = __fadd_rn(g[j], __fmul_rn(delta, __fadd_rn(p.S2[(int64_t)i * P + j], acc)));
+                }
+            } else {
+                for (int rr = p.bptr[i]; rr < p.bptr[i + 1]; ++rr) {
+                    float acc = 0.0f;
+                    for (int e = p.rbeg[rr]; e < p.rbeg[rr + 1]; ++e) {
+                        bool on = true;
+                        for (int q = 0; q < KU; ++q) {
+                            const int v = p.uconds[(int64_t)e * KU + q];
+                            if (v < N && !bit_of(x, v)) on = false;
+                        }
+                        if (on) acc = __fadd_rn(acc, p.ucoef[e]);
+                    }
+                    const int j = p.rtgt[rr];
+                    g[j] = __fadd_rn(g[j], __fmul_rn(delta, acc));
+                }
+            }
+            if (E < Eb) {
+                Eb = E;
+                for (int k = 0; k < W; ++k) bx[k] = x[k];
+            }
+        }
+    }
+    p.E[b] = E;
+    p.bestE[b] = Eb;
+    if (p.accepts) p.accepts[b] += nacc;
+}
+
+static SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
+{
+    SweepDev p{};
+    p.N = h->N; p.W = h->W; p.B = a.B; p.sweeps = a.sweeps; p.sweep0 = a.sweep0;
+    p.resume = a.resume; p.P = (h->N + 3) & ~3;
+    p.k0 = (uint32_t)a.seed; p.k1 = (uint32_t)(a.seed >> 32);
+    p.beta = a.beta; p.X = a.X; p.g = a.g; p.E = a.E; p.bestX = a.bestX; p.bestE = a.bestE;
+    p.accepts = a.accepts;
+    p.write_g = a.write_g ? 1 : 0;
+    p.bptr = h->d.bptr; p.rtgt = h->d.rtgt; p.rbeg = h->d.rbeg; p.ucoef = h->d.ucoef;
+    p.uconds = h->d.uconds; p.S2 = h->d.S2; p.S3 = h->d.S3;
+    return p;
+}
+
+cudaError_t launch_sweep_tuned(const hobo_instance* h, const SweepArgs& a, cudaStream_t st)
+{
+    if (a.B == 0 || a.sweeps == 0) return cudaSuccess;
+    const SweepDev p = make_dev(h, a);
+    if (h->dense) return dispatch_tuned<true, 1>(p, st);
+    if (h->KU <= 1) return dispatch_tuned<false, 1>(p, st);
+    if (h->KU <= 2) return dispatch_tuned<false, 2>(p, st);
+    return dispatch_tuned<false, 6>(p, st);
+}
+
+cudaError_t launch_sweep_plain(const hobo_instance* h, const SweepArgs& a, cudaStream_t st)
+{
+    if (a.B == 0 || a.sweeps == 0) return cudaSuccess;
+    const SweepDev p = make_dev(h, a);
+    const int threads = 128;
+    const unsigned grid = (unsigned)((a.B + threads - 1) / threads);
+    if (h->dense) sweep_plain_kernel<true, 1><<<grid, threads, 0, st>>>(p);
+    else if (h->KU <= 1) sweep_plain_kernel<false, 1><<<grid, threads, 0, st>>>(p);
+    else if (h->KU <= 2) sweep_plain_kernel<false, 2><<<grid, threads, 0, st>>>(p);
+    else sweep_plain_kernel<false, 6><<<grid, threads, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace hobo

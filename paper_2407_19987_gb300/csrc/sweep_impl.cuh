@@ -1,0 +1,271 @@
+// Metropolis sweep kernels (included by the sweep translation units).
+#pragma once
+#include "hobo_internal.h"
+#include "hobo_dev.cuh"
+
+namespace hobo {
+
+// ===========================================================================
+// Metropolis sweeps.
+//
+// Both kernels implement the same sequential semantics per state: for each
+// sweep s and each bit i = 0..N-1 in order, dE = (1 - 2 x_i) g_i, accept by
+// metropolis(dE, beta_s, word(i, s, state)); on accept flip x_i, E += dE,
+// and for every monomial containing i and another member j add
+// delta * c * (product of the remaining members) to g_j (delta = +1 for a
+// 0->1 flip, -1 for 1->0); keep the best state on strict improvement.
+// Update sums are formed in the same order in both kernels, so they agree
+// bit for bit on every instance, and with the CPU oracle on integer ones.
+// ===========================================================================
+struct SweepDev {
+    int N, W, B, sweeps, sweep0, resume, P;   // P: row pitch of the dense slab
+    int write_g;
+    uint32_t k0, k1;
+    const float* beta;
+    uint32_t* X;
+    float* g;
+    float* E;
+    uint32_t* bestX;
+    float* bestE;
+    int64_t* accepts;
+    const int32_t* bptr;
+    const int32_t* rtgt;
+    const int32_t* rbeg;
+    const float* ucoef;
+    const uint16_t* uconds;
+    const float* S2;     // [N][P]
+    const float* S3;     // [N][N][P]
+};
+
+template <int WMAX>
+__device__ __forceinline__ uint32_t sel_word(const uint32_t (&x)[WMAX], int w)
+{
+    uint32_t r = x[0];
+#pragma unroll
+    for (int k = 1; k < WMAX; ++k) r = (k == w) ? x[k] : r;
+    return r;
+}
+
+template <int WMAX>
+__device__ __forceinline__ void set_word(uint32_t (&x)[WMAX], int w, uint32_t v)
+{
+#pragma unroll
+    for (int k = 0; k < WMAX; ++k) x[k] = (k == w) ? v : x[k];
+}
+
+// ---------------------------------------------------------------------------
+// Tuned sweep: one warp per state.  The state's fields live in shared
+// memory; its bits are held (identically) in every lane's registers.  Bits
+// are visited a word at a time: lane t evaluates the decision for bit
+// 32w + t.  Until the first accepted bit f of the word nothing changes, so
+// the decisions of bits < f are final; bit f is then applied (fields
+// updated by the whole warp) and the word is re-evaluated from f + 1.  This
+// is exactly the sequential order of the definition.
+// ---------------------------------------------------------------------------
+constexpr int kSweepWarps = 8;
+
+// Dense order<=3 update for a flip of bit i: g_j += delta * (S2[i][j] +
+// sum_{l set} S3[i][l][j]).  Lanes own 4 consecutive targets per 128-wide
+// chunk; set rows l are visited in ascending order.
+template <int WMAX>
+__device__ __forceinline__ void dense_update(const SweepDev& p, float* __restrict__ g,
+                                             const uint32_t (&x)[WMAX], int i, float delta, int lane)
+{
+    const int N = p.N, P = p.P;
+    const float* __restrict__ slab = p.S3 + (int64_t)i * N * P;
+    for (int c0 = 0; c0 < P; c0 += 128) {
+        const int j = c0 + 4 * lane;
+        const bool jv = j < P;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int W = p.W;
+#pragma unroll 1
+        for (int k = 0; k < W; ++k) {
+            const uint32_t u = sel_word(x, k);
+#pragma unroll 1
+            for (int t0 = 0; t0 < 32; t0 += 8) {
+                if (((u >> t0) & 0xFFu) == 0u) continue;
+                float4 v[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int l = 32 * k + t0 + t;
+                    v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (jv && ((u >> (t0 + t)) & 1u))
+                        v[t] = __ldg(reinterpret_cast<const float4*>(slab + (int64_t)l * P + j));
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    if ((u >> (t0 + t)) & 1u) {
+                        acc.x = __fadd_rn(acc.x, v[t].x);
+                        acc.y = __fadd_rn(acc.y, v[t].y);
+                        acc.z = __fadd_rn(acc.z, v[t].z);
+                        acc.w = __fadd_rn(acc.w, v[t].w);
+                    }
+                }
+            }
+        }
+        if (jv) {
+            const float4 s2 = __ldg(reinterpret_cast<const float4*>(p.S2 + (int64_t)i * P + j));
+            const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
+            const float s4[4] = {s2.x, s2.y, s2.z, s2.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j + q < N)
+                    g[j + q] = __fadd_rn(g[j + q], __fmul_rn(delta, __fadd_rn(s4[q], a4[q])));
+        }
+    }
+}
+
+// Sparse update for a flip of bit i: lanes take target records; each sums
+// the coefficients of its entries whose conditions are all set.
+template <int KU>
+__device__ __forceinline__ void sparse_update(const SweepDev& p, float* __restrict__ g,
+                                              const uint32_t* __restrict__ bs, int i, float delta,
+                                              int lane)
+{
+    const int r0 = p.bptr[i], r1 = p.bptr[i + 1];
+    for (int r = r0 + lane; r < r1; r += 32) {
+        const int j = p.rtgt[r];
+        const int e0 = p.rbeg[r], e1 = p.rbeg[r + 1];
+        float acc = 0.0f;
+        for (int e = e0; e < e1; ++e) {
+            const float c = p.ucoef[e];
+            uint32_t pr = 1u;
+#pragma unroll
+            for (int s = 0; s < KU; ++s) {
+                const int v = p.uconds[(int64_t)e * KU + s];
+                pr &= bs[v >> 5] >> (v & 31);
+            }
+            if (pr & 1u) acc = __fadd_rn(acc, c);
+        }
+        g[j] = __fadd_rn(g[j], __fmul_rn(delta, acc));
+    }
+}
+
+template <int WMAX, bool DENSE, int KU>
+__global__ void __launch_bounds__(kSweepWarps * 32)
+sweep_tuned_kernel(const SweepDev p)
+{
+    extern __shared__ float sm[];
+    const int N = p.N, W = p.W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x * kSweepWarps + warp;       // state of this warp
+    if (b >= p.B) return;                                // warp-uniform; no block barriers below
+    const int NPAD = (N + 3) & ~3;
+    float* g = sm + (size_t)warp * (NPAD + 4 * (WMAX + 1));
+    uint32_t* bs = reinterpret_cast<uint32_t*>(g + NPAD);   // bits + sentinel (sparse lookups)
+
+    for (int j = lane; j < N; j += 32) g[j] = p.g[(int64_t)b * N + j];
+    uint32_t x[WMAX], bx[WMAX];
+#pragma unroll
+    for (int k = 0; k < WMAX; ++k) {
+        uint32_t v = (k < W) ? p.X[(int64_t)b * W + k] : 0u;
+        const int rem = N - 32 * k;
+        if (rem <= 0) v = 0u; else if (rem < 32) v &= (1u << rem) - 1u;
+        x[k] = v;
+    }
+    float E = p.E[b], Eb = E;
+#pragma unroll
+    for (int k = 0; k < WMAX; ++k) bx[k] = x[k];
+    if (p.resume) {
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) bx[k] = (k < W) ? p.bestX[(int64_t)b * W + k] : 0u;
+        Eb = p.bestE[b];
+    }
+    const int wsent = N >> 5;
+    const uint32_t sent = 1u << (N & 31);
+    if (!DENSE) {
+        for (int k = lane; k <= W; k += 32) {
+            uint32_t v = (k < W) ? sel_word(x, k) : 0u;
+            if (k == wsent) v |= sent;
+            bs[k] = v;
+        }
+    }
+    __syncwarp();
+
+    long long nacc = 0;
+    for (int s = 0; s < p.sweeps; ++s) {
+        const float beta = __ldg(p.beta + s);
+        const uint32_t sw = (uint32_t)(p.sweep0 + s);
+        for (int w = 0; w < W; ++w) {
+            uint32_t cw = sel_word(x, w);
+            const int nbits = min(32, N - 32 * w);
+            // the draw of bit 32w + lane: word (lane % 4) of counter (8w + lane/4, s, b, 0)
+            const u32x4 r = philox10((uint32_t)(8 * w + (lane >> 2)), sw, (uint32_t)b,
+                                     kStreamMetropolis, p.k0, p.k1);
+            const uint32_t rw = pick4(r, lane & 3);
+            int t0 = 0;
+            while (true) {
+                const int i = 32 * w + lane;
+                bool acc = false;
+                float dE = 0.0f;
+                if (lane >= t0 && lane < nbits) {
+                    const float gi = g[i];
+                    dE = ((cw >> lane) & 1u) ? -gi : gi;
+                    acc = metropolis(dE, beta, rw);
+                }
+                const uint32_t m = __ballot_sync(0xffffffffu, acc);
+                if (m == 0u) break;
+                const int f = __ffs(m) - 1;
+                const float dEf = __shfl_sync(0xffffffffu, dE, f);
+                const float delta = ((cw >> f) & 1u) ? -1.0f : 1.0f;
+                cw ^= 1u << f;
+                E = __fadd_rn(E, dEf);
+                ++nacc;
+                set_word(x, w, cw);
+                if (E < Eb) {
+                    Eb = E;
+#pragma unroll
+                    for (int k = 0; k < WMAX; ++k) bx[k] = x[k];
+                }
+                const int fi = 32 * w + f;
+                if (DENSE) {
+                    dense_update<WMAX>(p, g, x, fi, delta, lane);
+                } else {
+                    if (lane == 0) bs[w] = cw | (w == wsent ? sent : 0u);
+                    __syncwarp();
+                    sparse_update<KU>(p, g, bs, fi, delta, lane);
+                }
+                __syncwarp();
+                t0 = f + 1;
+                if (t0 >= nbits) break;
+            }
+            set_word(x, w, cw);
+        }
+    }
+
+    for (int k = lane; k < W; k += 32) {
+        p.X[(int64_t)b * W + k] = sel_word(x, k);
+        p.bestX[(int64_t)b * W + k] = sel_word(bx, k);
+    }
+    if (p.write_g)
+        for (int j = lane; j < N; j += 32) p.g[(int64_t)b * N + j] = g[j];
+    if (lane == 0) {
+        p.E[b] = E;
+        p.bestE[b] = Eb;
+        if (p.accepts) p.accepts[b] += nacc;
+    }
+}
+
+template <int WMAX, bool DENSE, int KU>
+inline cudaError_t run_tuned(const SweepDev& p, cudaStream_t st)
+{
+    const int NPAD = (p.N + 3) & ~3;
+    const size_t per_warp = sizeof(float) * (size_t)(NPAD + 4 * (WMAX + 1));
+    const size_t sm = per_warp * kSweepWarps;
+    auto kern = sweep_tuned_kernel<WMAX, DENSE, KU>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((p.B + kSweepWarps - 1) / kSweepWarps);
+    kern<<<grid, kSweepWarps * 32, sm, st>>>(p);
+    return cudaGetLastError();
+}
+
+
+template <bool DENSE, int KU>
+cudaError_t dispatch_tuned(const SweepDev& p, cudaStream_t st);
+template <> cudaError_t dispatch_tuned<true, 1>(const SweepDev& p, cudaStream_t st);
+template <> cudaError_t dispatch_tuned<false, 1>(const SweepDev& p, cudaStream_t st);
+template <> cudaError_t dispatch_tuned<false, 2>(const SweepDev& p, cudaStream_t st);
+template <> cudaError_t dispatch_tuned<false, 6>(const SweepDev& p, cudaStream_t st);
+
+}  // namespace hobo

@@ -1,0 +1,17 @@
+// Instantiations of the tuned sweep kernel: term lists, up to one condition per entry (order <= 3).
+#include "sweep_impl.cuh"
+
+namespace hobo {
+
+template <>
+cudaError_t dispatch_tuned<false, 1>(const SweepDev& p, cudaStream_t st)
+{
+    if (p.W <= 1) return run_tuned<1, false, 1>(p, st);
+    if (p.W <= 2) return run_tuned<2, false, 1>(p, st);
+    if (p.W <= 4) return run_tuned<4, false, 1>(p, st);
+    if (p.W <= 8) return run_tuned<8, false, 1>(p, st);
+    if (p.W <= 16) return run_tuned<16, false, 1>(p, st);
+    return run_tuned<32, false, 1>(p, st);
+}
+
+}  // namespace hobo

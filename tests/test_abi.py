@@ -1,0 +1,105 @@
+"""The C ABI library loads, exports every symbol include/hobo.h declares, and
+rejects bad arguments on the host (no GPU work).  CPU only."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2407_19987_gb300 as H
+from paper_2407_19987_gb300 import binding as Bd
+from paper_2407_19987_gb300 import build as Bld
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(Bd.LIB_PATH):
+        Bld.build()
+    return H.load_library()
+
+
+def declared_symbols():
+    out = set()
+    for name in os.listdir(os.path.join(ROOT, "include")):
+        if not name.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", name)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(hobo_[a-z0-9_]+)\s*\(", src):
+            out.add(m.group(1))
+    return out
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert {"hobo_create", "hobo_create_terms", "hobo_energy", "hobo_anneal", "hobo_destroy",
+            "hobo_last_error"} <= syms
+    for s in sorted(syms):
+        assert hasattr(lib, s), s
+
+
+def test_version(lib):
+    assert H.version().startswith("hobo-gb300")
+
+
+def test_create_rejects_bad_arguments(lib):
+    h = C.c_void_p(123)
+    T = np.zeros(8, np.float32)
+    assert lib.hobo_create(None, T.ctypes.data_as(C.c_void_p), 3, 2, 0) == Bd.HOBO_ERR_ARG
+    assert lib.hobo_create(C.byref(h), None, 3, 2, 0) == Bd.HOBO_ERR_ARG
+    assert h.value is None
+    assert lib.hobo_create(C.byref(h), T.ctypes.data_as(C.c_void_p), 0, 2, 0) == Bd.HOBO_ERR_ORDER
+    assert lib.hobo_create(C.byref(h), T.ctypes.data_as(C.c_void_p), 9, 2, 0) == Bd.HOBO_ERR_ORDER
+    assert lib.hobo_create(C.byref(h), T.ctypes.data_as(C.c_void_p), 3, 0, 0) == Bd.HOBO_ERR_ARG
+    assert lib.hobo_create(C.byref(h), T.ctypes.data_as(C.c_void_p), 3, 1025, 0) == Bd.HOBO_ERR_ARG
+    assert b"N must be" in lib.hobo_last_error()
+
+
+def test_create_terms_index_checks(lib):
+    h = C.c_void_p()
+    idx = np.array([[0, 1, 5]], np.int32)
+    coef = np.ones(1, np.float32)
+    rc = lib.hobo_create_terms(C.byref(h), idx.ctypes.data_as(C.c_void_p), coef.ctypes.data_as(C.c_void_p),
+                               1, 3, 5, 0)
+    assert rc == Bd.HOBO_ERR_ARG and b"out of range" in lib.hobo_last_error()
+    idx = np.array([[0, -1, 2]], np.int32)
+    rc = lib.hobo_create_terms(C.byref(h), idx.ctypes.data_as(C.c_void_p), coef.ctypes.data_as(C.c_void_p),
+                               1, 3, 5, 0)
+    assert rc == Bd.HOBO_ERR_ARG
+    bad = np.array([np.nan], np.float32)
+    idx = np.array([[0, 1, 2]], np.int32)
+    rc = lib.hobo_create_terms(C.byref(h), idx.ctypes.data_as(C.c_void_p), bad.ctypes.data_as(C.c_void_p),
+                               1, 3, 5, 0)
+    assert rc == Bd.HOBO_ERR_ARG
+    rc = lib.hobo_create_terms(C.byref(h), None, None, 1, 3, 5, 0)
+    assert rc == Bd.HOBO_ERR_ARG
+
+
+def test_integer_flag_checks_on_host(lib):
+    """HOBO_INTEGER is refused before any device work when coefficients are
+    not integers or their absolute sum reaches 2^24."""
+    h = C.c_void_p()
+    idx = np.array([[0, 1, 2], [1, 1, 2]], np.int32)
+    frac = np.array([1.5, 2.0], np.float32)
+    rc = lib.hobo_create_terms(C.byref(h), idx.ctypes.data_as(C.c_void_p), frac.ctypes.data_as(C.c_void_p),
+                               2, 3, 3, Bd.HOBO_INTEGER)
+    assert rc == Bd.HOBO_ERR_NOT_EXACT
+    big = np.array([2.0 ** 23, 2.0 ** 23], np.float32)
+    rc = lib.hobo_create_terms(C.byref(h), idx.ctypes.data_as(C.c_void_p), big.ctypes.data_as(C.c_void_p),
+                               2, 3, 3, Bd.HOBO_INTEGER)
+    assert rc == Bd.HOBO_ERR_NOT_EXACT and b"2^24" in lib.hobo_last_error()
+    # folding makes +3 and -3 cancel: nothing left, still integer-exact (no GPU
+    # work is reached only if the instance is refused; here it is accepted and
+    # the device query fails without a GPU, or succeeds with one)
+
+
+def test_null_instance_calls(lib):
+    assert lib.hobo_energy(None, None, 0, None, None, None) == Bd.HOBO_ERR_ARG
+    assert lib.hobo_energy_fp64(None, None, 0, None, None) == Bd.HOBO_ERR_ARG
+    assert lib.hobo_anneal(None, 0, 0, None, 0, None, None, None, None) == Bd.HOBO_ERR_ARG
+    assert lib.hobo_info(None, None) == Bd.HOBO_ERR_ARG
+    lib.hobo_destroy(None)

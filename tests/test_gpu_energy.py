@@ -1,0 +1,153 @@
+"""GPU parity of the batched contraction (hobo_energy, hobo_energy_fp64)
+against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import gpuh
+import polyexp
+import workloads as W
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_int(inst, X, flags=0, path=0):
+    import paper_2407_19987_gb300 as H
+    h = gpuh.make(inst, flags)
+    Xd = gpuh.to_dev(X)
+    E, dE = h.energy(Xd, path=path)
+    E = E.cpu().numpy().astype(np.float64)
+    dE = dE.cpu().numpy().astype(np.float64)
+    refE = O.energy_int(inst, X).astype(np.float64)
+    np.testing.assert_array_equal(E, refE)
+    for b in range(X.shape[0]):
+        g = O.fields(inst, X[b])
+        np.testing.assert_array_equal(dE[b], (1.0 - 2.0 * X[b]) * g)
+    E64 = h.energy_fp64(Xd).cpu().numpy()
+    np.testing.assert_array_equal(E64, refE)
+    h.close()
+
+
+INT_CASES = [
+    ("tiny_dense", lambda: W.tiny_dense(1)),
+    ("order1_N1", lambda: W.Instance(1, 1, np.array([[0]], np.int32), np.array([-3], np.float32), integer=True)),
+    ("order2_N33", lambda: W.random_sparse(31, 33, 2, 0.4, "int")),
+    ("order3_N32", lambda: W.random_sparse(32, 32, 3, 0.2, "int")),
+    ("order3_N70", lambda: W.random_sparse(33, 70, 3, 0.05, "int")),
+    ("order4_N40", lambda: W.random_sparse(34, 40, 4, 0.02, "int")),
+    ("order5_N20", lambda: W.random_sparse(35, 20, 5, 0.05, "int")),
+    ("order6_N16", lambda: W.random_sparse(36, 16, 6, 0.05, "int")),
+    ("pythagorean", polyexp.pythagorean),
+    ("tsp", polyexp.tsp_intenc),
+    ("seating", polyexp.seating),
+    ("int_encoded", lambda: W.int_encoded(3)),
+]
+
+
+@pytest.mark.parametrize("name,maker", INT_CASES, ids=[c[0] for c in INT_CASES])
+@pytest.mark.parametrize("B", [1, 33, 100])
+def test_energy_integer_exact(name, maker, B):
+    inst = maker()
+    X = W.random_states(100 + B, B, inst.N)
+    _check_int(inst, X)
+
+
+def test_energy_dense_int_forced_dense():
+    inst = W.random_sparse(40, 64, 3, 0.5, "int")
+    X = W.random_states(41, 77, inst.N)
+    _check_int(inst, X, flags=4)   # HOBO_FORCE_DENSE
+
+
+def test_energy_dense_entries_below_diagonal():
+    """hobo_create folds every entry of a full dense tensor (not only the
+    upper part) onto its distinct index set."""
+    import paper_2407_19987_gb300 as H
+    rng = np.random.default_rng(5)
+    N, k = 9, 3
+    T = rng.integers(-5, 6, size=(N,) * k).astype(np.float32)
+    grid = np.stack(np.meshgrid(*[np.arange(N)] * k, indexing="ij"), -1).reshape(-1, k).astype(np.int32)
+    inst = W.Instance(N, k, grid, T.reshape(-1), integer=True)
+    h = H.Instance.from_dense(T)
+    X = W.random_states(6, 40, N)
+    E, dE = h.energy(gpuh.to_dev(X))
+    np.testing.assert_array_equal(E.cpu().numpy(), O.energy_int(inst, X).astype(np.float32))
+    for b in range(40):
+        np.testing.assert_array_equal(dE[b].cpu().numpy(), ((1.0 - 2.0 * X[b]) * O.fields(inst, X[b])).astype(np.float32))
+
+
+FLOAT_CASES = [
+    ("order3_sparse", lambda: W.random_sparse(50, 90, 3, 0.1, "normal")),
+    ("order4_sparse", lambda: W.random_sparse(51, 48, 4, 0.05, "normal")),
+    ("order3_dense_N48", lambda: W.dense_float(52, 48)),
+    ("order2_N200", lambda: W.random_sparse(53, 200, 2, 0.5, "normal")),
+]
+
+
+@pytest.mark.parametrize("name,maker", FLOAT_CASES, ids=[c[0] for c in FLOAT_CASES])
+@pytest.mark.parametrize("path", [0, 1])
+def test_energy_float_within_tolerance(name, maker, path):
+    inst = maker()
+    h = gpuh.make(inst)
+    X = W.random_states(60, 70, inst.N)
+    E, dE = h.energy(gpuh.to_dev(X), path=path)
+    E = E.cpu().numpy().astype(np.float64)
+    dE = dE.cpu().numpy().astype(np.float64)
+    absi = gpuh.abs_instance(inst)
+    refE = O.energy(inst, X)
+    assert gpuh.rel_err(E, refE, O.energy(absi, X)).max() <= gpuh.FLOAT_RTOL
+    for b in range(X.shape[0]):
+        g = O.fields(inst, X[b])
+        ga = O.fields(absi, X[b])
+        assert gpuh.rel_err(dE[b], (1.0 - 2.0 * X[b]) * g, ga).max() <= gpuh.FLOAT_RTOL
+    E64 = h.energy_fp64(gpuh.to_dev(X)).cpu().numpy()
+    np.testing.assert_allclose(E64, refE, rtol=1e-12, atol=1e-9)
+
+
+def test_energy_dense_float_full_size_sampled():
+    """Dense order-3 N=256 float instance, B=4096 states in one call; a
+    sample of states is checked against the oracle."""
+    inst = W.dense_float(2)
+    h = gpuh.make(inst)
+    B = 4096
+    X = W.random_states(61, B, inst.N)
+    E, dE = h.energy(gpuh.to_dev(X))
+    E = E.cpu().numpy().astype(np.float64)
+    dE = dE.cpu().numpy().astype(np.float64)
+    absi = gpuh.abs_instance(inst)
+    rng = np.random.default_rng(0)
+    sample = np.concatenate([[0, 1, 127, 128, B - 1], rng.choice(B, 11, replace=False)])
+    refE = O.energy(inst, X[sample])
+    assert gpuh.rel_err(E[sample], refE, O.energy(absi, X[sample])).max() <= gpuh.FLOAT_RTOL
+    for b in sample[:6]:
+        g = O.fields(inst, X[b])
+        assert gpuh.rel_err(dE[b], (1.0 - 2.0 * X[b]) * g, O.fields(absi, X[b])).max() <= gpuh.FLOAT_RTOL
+
+
+def test_energy_wide_instance_N1024():
+    inst = W.random_sparse(70, 1024, 2, 0.002, "int")
+    X = W.random_states(71, 5, inst.N)
+    _check_int(inst, X)
+
+
+def test_energy_empty_batch_and_no_delta():
+    import torch
+    inst = W.tiny_dense(1)
+    h = gpuh.make(inst)
+    X = torch.zeros((0, 1), dtype=torch.int32, device="cuda")
+    E, dE = h.energy(X)
+    assert E.numel() == 0
+    Xs = W.random_states(3, 10, inst.N)
+    E, dE = h.energy(gpuh.to_dev(Xs), with_delta=False)
+    assert dE is None
+    np.testing.assert_array_equal(E.cpu().numpy(), O.energy_int(inst, Xs).astype(np.float32))
+
+
+def test_energy_ignores_bits_beyond_N():
+    inst = W.random_sparse(80, 37, 3, 0.1, "int")
+    X = W.random_states(81, 20, inst.N)
+    P = W.pack_bits(X)
+    P[:, -1] |= np.uint32(0xFFFFFFFF) << np.uint32(37 - 32)
+    import torch
+    h = gpuh.make(inst)
+    E, dE = h.energy(torch.from_numpy(P.view(np.int32)).cuda())
+    np.testing.assert_array_equal(E.cpu().numpy(), O.energy_int(inst, X).astype(np.float32))
