@@ -52,9 +52,15 @@ extern "C" {
                                  every float32 partial sum is exact */
 #define HOBO_FORCE_SPARSE 2u  /* use the term-list layouts even if dense */
 #define HOBO_FORCE_DENSE  4u  /* build the dense slab layout (order <= 3) */
-#define HOBO_SPLIT3       8u  /* tensor-core energy: hi+mid+lo bf16 split
-                                 (exact for float32 coefficients) instead of
-                                 hi+lo */
+#define HOBO_SPLIT3       8u  /* tensor-core energy: always use the hi+mid+lo
+                                 bf16 split (the default for non-integer
+                                 coefficients; exact for float32 values) */
+#define HOBO_SPLIT2      16u  /* tensor-core energy: hi+lo bf16 split for
+                                 non-integer coefficients (relative error per
+                                 coefficient <= 2^-17; faster, below the
+                                 1e-5 bar on ill-conditioned fields).  Integer
+                                 coefficients below 2^16 always use hi+lo,
+                                 which is exact for them. */
 
 typedef struct hobo_instance* hobo_h;
 
@@ -127,9 +133,13 @@ int hobo_energy_path(hobo_h h, const uint32_t* X, int B, float* E, float* dE, in
                      void* stream);
 
 /*
- * hobo_energy_fp64 -- the energies of B packed states summed in float64
- * over the folded coefficients (kept in float64), for re-scoring reported
- * states.  X device uint32 [B][W]; E device double [B].
+ * hobo_energy_fp64 -- float64 energies of B packed states, for re-scoring
+ * reported states.  The folded coefficients are held as exact 64-bit
+ * fixed-point integers round(c * 2^S), S chosen per instance so that no
+ * partial sum can overflow; each energy is the exact integer sum over the
+ * active monomials, rounded once to float64.  Exact for integer instances;
+ * otherwise the error is below that of a float64 summation.
+ * X device uint32 [B][W]; E device double [B].
  */
 int hobo_energy_fp64(hobo_h h, const uint32_t* X, int B, double* E, void* stream);
 
@@ -185,6 +195,15 @@ typedef struct {
  */
 int hobo_anneal(hobo_h h, uint64_t seed, int B, const float* beta, int sweeps,
                 uint32_t* bestX, double* bestE, const hobo_anneal_opts* opts, void* stream);
+
+/*
+ * hobo_check -- wait for the work enqueued on `stream` and report whether
+ * any kernel of this instance gave up a bounded device-side wait since the
+ * last check (HOBO_ERR_TIMEOUT; the status is cleared).  Waits in the
+ * library's kernels are time-limited, so a stall ends the kernel instead of
+ * hanging the GPU.  Errors: HOBO_ERR_ARG, HOBO_ERR_CUDA, HOBO_ERR_TIMEOUT.
+ */
+int hobo_check(hobo_h h, void* stream);
 
 /* Human-readable message of the last error on this thread ("" if none). */
 const char* hobo_last_error(void);

@@ -28,6 +28,7 @@ HOBO_INTEGER = 1
 HOBO_FORCE_SPARSE = 2
 HOBO_FORCE_DENSE = 4
 HOBO_SPLIT3 = 8
+HOBO_SPLIT2 = 16
 
 HOBO_ANNEAL_TUNED = 0
 HOBO_ANNEAL_PLAIN = 1
@@ -77,10 +78,11 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     L.hobo_energy_path.argtypes = [P, P, I, P, P, I, P]
     L.hobo_energy_fp64.argtypes = [P, P, I, P, P]
     L.hobo_anneal.argtypes = [P, U64, I, P, I, P, P, C.POINTER(hobo_anneal_opts), P]
+    L.hobo_check.argtypes = [P, P]
     L.hobo_last_error.restype = C.c_char_p
     L.hobo_version.restype = C.c_char_p
     for name in ("hobo_create", "hobo_create_terms", "hobo_info", "hobo_energy", "hobo_energy_path",
-                 "hobo_energy_fp64", "hobo_anneal"):
+                 "hobo_energy_fp64", "hobo_anneal", "hobo_check"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -169,6 +171,11 @@ class Instance:
     def energy_into(self, X, E, dE=None, path: int = PATH_AUTO, stream=None):
         _check(load_library().hobo_energy_path(self._h, _ptr(X), X.shape[0], _ptr(E), _ptr(dE), path,
                                                _stream(stream)))
+
+    def check(self, stream=None):
+        """Synchronize the stream and raise HoboError(HOBO_ERR_TIMEOUT) if a
+        kernel of this instance gave up a bounded wait."""
+        _check(load_library().hobo_check(self._h, _stream(stream)))
 
     def energy_fp64(self, X, stream=None):
         import torch

@@ -92,8 +92,8 @@ static int upload(T** dst, const std::vector<T>& src)
 
 static void free_layouts(DevLayouts& d)
 {
-    void* ptrs[] = {d.tvars, d.tcoef32, d.tcoef64, d.fptr, d.fvars, d.fcoef, d.bptr, d.rtgt,
-                    d.rbeg, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3bf[0], d.S3bf[1], d.S3bf[2]};
+    void* ptrs[] = {d.tvars, d.tcoef32, d.tcoef64, d.tfix, d.fptr, d.fvars, d.fcoef, d.bptr, d.rtgt,
+                    d.rbeg, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DevLayouts{};
@@ -134,6 +134,8 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
     // condition slots per update entry: the sweep kernels are compiled for
     // 1, 2 or 6 slots, so the layout stride is rounded up to one of those
     h->KU = K <= 3 ? 1 : (K == 4 ? 2 : 6);
+    // variable slots per monomial in the monomial list (8- or 16-byte rows)
+    h->KS = K <= 4 ? 4 : 8;
     h->W = (N + 31) / 32;
 
     double abs_sum = 0.0, maxabs = 0.0;
@@ -156,17 +158,28 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
 
     // (1) monomial list
     {
-        std::vector<uint16_t> tv((size_t)M * K);
+        const int KS = h->KS;
+        std::vector<uint16_t> tv((size_t)std::max<int64_t>(M, 1) * KS, (uint16_t)N);
         std::vector<float> c32((size_t)M);
         std::vector<double> c64((size_t)M);
+        std::vector<long long> cfix((size_t)M);
+        // fixed-point scale: sum |c| * 2^S < 2^62 keeps every partial sum in range
+        int S = 0;
+        if (abs_sum > 0.0) {
+            int ex;
+            std::frexp(abs_sum, &ex);          // abs_sum < 2^ex
+            S = 62 - ex;
+        }
+        d.fix_shift = S;
         for (int64_t t = 0; t < M; ++t) {
-            for (int q = 0; q < K; ++q)
-                tv[(size_t)t * K + q] = q < mono[t].m.d ? mono[t].m.v[q] : (uint16_t)N;
+            for (int q = 0; q < mono[t].m.d; ++q) tv[(size_t)t * KS + q] = mono[t].m.v[q];
             c32[t] = (float)mono[t].c;
             c64[t] = mono[t].c;
+            cfix[t] = std::llrint(std::ldexp(mono[t].c, S));
         }
         int rc;
-        if ((rc = upload(&d.tvars, tv)) || (rc = upload(&d.tcoef32, c32)) || (rc = upload(&d.tcoef64, c64)))
+        if ((rc = upload(&d.tvars, tv)) || (rc = upload(&d.tcoef32, c32)) || (rc = upload(&d.tcoef64, c64)) ||
+            (rc = upload(&d.tfix, cfix)))
             return rc;
     }
     // (2) field list by variable
@@ -220,29 +233,50 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
                     S3[((size_t)v[pm[0]] * N + v[pm[1]]) * P + v[pm[2]]] = c;
             }
         }
+        std::vector<double> colsum((size_t)N * P, 0.0);
+        for (auto& e : mono)
+            if (e.m.d == 3) {
+                const int v[3] = {e.m.v[0], e.m.v[1], e.m.v[2]};
+                // slab i, column j collects c over the third member l
+                for (int q = 0; q < 3; ++q)
+                    for (int r = 0; r < 3; ++r)
+                        if (q != r) colsum[(size_t)v[q] * P + v[r]] += (double)(float)e.c;
+            }
+        std::vector<float> S3col(colsum.begin(), colsum.end());
         int rc;
-        if ((rc = upload(&d.a, a)) || (rc = upload(&d.S2, S2)) || (rc = upload(&d.S3, S3))) return rc;
+        if ((rc = upload(&d.a, a)) || (rc = upload(&d.S2, S2)) || (rc = upload(&d.S3, S3)) ||
+            (rc = upload(&d.S3col, S3col)))
+            return rc;
 
-        // bf16 split planes for the tensor-core contraction: [m][j][l] with
-        // K (= l) pitch KP = N rounded up to 64, rows m*N + j.
-        int nsplit = 2;
-        if ((flags & HOBO_SPLIT3) || (h->integer && maxabs >= 65536.0)) nsplit = 3;
-        d.nsplit = nsplit;
-        const int KP = (N + 63) & ~63;
-        std::vector<uint16_t> planes[3];
-        for (int q = 0; q < nsplit; ++q) planes[q].assign((size_t)N * N * KP, 0);
-        for (auto& e : mono) {
-            if (e.m.d != 3) continue;
-            uint16_t sp[3];
-            choose_split(e.c, nsplit, sp);
-            const int v[3] = {e.m.v[0], e.m.v[1], e.m.v[2]};
-            const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-            for (auto& pm : perm)
-                for (int q = 0; q < nsplit; ++q)
-                    planes[q][((size_t)v[pm[0]] * N + v[pm[1]]) * KP + v[pm[2]]] = sp[q];
+        // bf16 split planes for the tensor-core contraction (N <= 256):
+        // [q][m][j][l], rows (m, j) padded to NJ, K = l padded to KP.
+        if (N <= 256) {
+            // two planes represent integers below 2^16 exactly; float
+            // coefficients need three (8+8+8 bits cover float32's 24)
+            int nsplit = 3;
+            if (h->integer && maxabs < 65536.0 && !(flags & HOBO_SPLIT3)) nsplit = 2;
+            if (!h->integer && (flags & HOBO_SPLIT2)) nsplit = 2;
+            d.nsplit = nsplit;
+            d.NJ = (N + 15) & ~15;
+            d.KP = (N + 63) & ~63;
+            const size_t plane = (size_t)N * d.NJ * d.KP;
+            std::vector<uint16_t> planes(plane * nsplit, 0);
+            for (auto& e : mono) {
+                if (e.m.d != 3) continue;
+                uint16_t sp[3];
+                choose_split(e.c, nsplit, sp);
+                const int v[3] = {e.m.v[0], e.m.v[1], e.m.v[2]};
+                const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+                for (auto& pm : perm)
+                    for (int q = 0; q < nsplit; ++q)
+                        planes[q * plane + ((size_t)v[pm[0]] * d.NJ + v[pm[1]]) * d.KP + v[pm[2]]] = sp[q];
+            }
+            if ((rc = upload(&d.S3bf, planes))) return rc;
+            if (make_tc_tensor_map(h) != cudaSuccess) {
+                (void)cudaGetLastError();
+                d.tmap_ok = false;
+            }
         }
-        for (int q = 0; q < nsplit; ++q)
-            if ((rc = upload(&d.S3bf[q], planes[q]))) return rc;
     } else {
         // (3) update lists grouped by (flipped bit i, target j)
         const int KU = h->KU;
@@ -331,10 +365,15 @@ static int create_from_entries(hobo_h* out, std::vector<Entry>& ent, int order, 
     if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+    e = cudaMalloc((void**)&h->status, sizeof(int));
+    if (e != cudaSuccess) { delete h; return fail(HOBO_ERR_OOM, "cudaMalloc status"); }
+    e = cudaMemset(h->status, 0, sizeof(int));
+    if (e != cudaSuccess) { cudaFree(h->status); delete h; return cuda_fail(e, "cudaMemset"); }
     const int rc = build_instance(h, mono, flags);
     if (rc != HOBO_OK) {
         const std::string msg = g_err;
         free_layouts(h->d);
+        cudaFree(h->status);
         delete h;
         set_error(msg);
         return rc;
@@ -416,7 +455,24 @@ void hobo_destroy(hobo_h h)
 {
     if (!h) return;
     free_layouts(h->d);
+    if (h->status) cudaFree(h->status);
     delete h;
+}
+
+int hobo_check(hobo_h h, void* stream)
+{
+    if (!h) return fail(HOBO_ERR_ARG, "NULL instance");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int v = 0;
+    e = cudaMemcpy(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (v != 0) {
+        const int zero = 0;
+        cudaMemcpy(h->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return fail(HOBO_ERR_TIMEOUT, "a device-side wait gave up (status " + std::to_string(v) + ")");
+    }
+    return HOBO_OK;
 }
 
 int hobo_info(hobo_h h, hobo_info_t* info)

@@ -10,12 +10,14 @@ namespace hobo {
 // Device copies of one instance's layouts.  All arrays are owned by the
 // instance and freed by hobo_destroy.
 struct DevLayouts {
-    // (1) folded monomial list, all degrees, `K = order` variable slots per
+    // (1) folded monomial list, all degrees, KS (4 or 8) variable slots per
     //     monomial padded with the sentinel index N (whose bit reads as 1).
     int64_t M = 0;
-    uint16_t* tvars = nullptr;   // [M][K]
+    uint16_t* tvars = nullptr;   // [M][KS]
     float* tcoef32 = nullptr;    // [M]
     double* tcoef64 = nullptr;   // [M]
+    long long* tfix = nullptr;   // [M] round(c * 2^fix_shift), exact re-score
+    int fix_shift = 0;
 
     // (2) field list by variable: entry e of variable j holds the
     //     coefficient of a monomial containing j and its other members
@@ -42,20 +44,26 @@ struct DevLayouts {
     float* a = nullptr;
     float* S2 = nullptr;
     float* S3 = nullptr;
-    uint16_t* S3bf[3] = {nullptr, nullptr, nullptr};
-    int nsplit = 0;
+    float* S3col = nullptr;      // [N][P]: S3col[i][j] = sum_l S3[i][l][j]
+    // bf16 planes [nsplit][N][NJ][KP]: plane q, row (m, j), column l;
+    // NJ = N rounded up to 16, KP = N rounded up to 64, zero padded.
+    uint16_t* S3bf = nullptr;
+    int nsplit = 0, NJ = 0, KP = 0;
+    alignas(64) unsigned char tmap[128] = {};   // CUtensorMap of the planes
+    bool tmap_ok = false;
 };
 
 }  // namespace hobo
 
 struct hobo_instance {
     int N = 0, order = 0, W = 0;
-    int KF = 1, KU = 1;
+    int KF = 1, KU = 1, KS = 4;
     bool dense = false, integer = false;
     int64_t terms[HOBO_MAX_ORDER + 1] = {0};
     double abs_sum = 0.0;
     int device = 0;
     int num_sms = 0;
+    int* status = nullptr;   // device status word written by kernels that give up a wait
     hobo::DevLayouts d;
 };
 
@@ -91,6 +99,8 @@ cudaError_t launch_sweep_plain(const hobo_instance* h, const SweepArgs& a, cudaS
 // instance has no dense layout.
 cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, float* E,
                              float* g_or_dE, bool flip_out, cudaStream_t st);
+bool tc_supported(const hobo_instance* h);
+cudaError_t make_tc_tensor_map(hobo_instance* h);
 
 void set_error(const std::string& msg);
 

@@ -2,6 +2,7 @@
 // contraction (float32), float64 re-scoring, and the Metropolis sweeps
 // (tuned warp-per-state kernel and the plain thread-per-state kernel).
 #include <algorithm>
+#include <type_traits>
 #include "hobo_internal.h"
 #include "hobo_dev.cuh"
 #include "sweep_impl.cuh"
@@ -66,7 +67,7 @@ energy_terms_kernel(const uint32_t* __restrict__ X, int B, int N, int W,
                     const int64_t* __restrict__ fptr, const uint16_t* __restrict__ fvars,
                     const float* __restrict__ fcoef, int KF,
                     const uint16_t* __restrict__ tvars, const float* __restrict__ tcoef,
-                    int64_t M, int K, float* __restrict__ out_g, float* __restrict__ out_E)
+                    int64_t M, int K, int KS, float* __restrict__ out_g, float* __restrict__ out_E)
 {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -114,7 +115,7 @@ energy_terms_kernel(const uint32_t* __restrict__ X, int B, int N, int W,
         const float c = tcoef[t];
         uint32_t p = 1u;
         for (int s = 0; s < K; ++s) {
-            const int v = tvars[t * K + s];
+            const int v = tvars[t * KS + s];
             p &= bits[(v >> 5) * 32 + lane] >> (v & 31);
         }
         if (p & 1u) kahan_add(eacc, ecomp, c);
@@ -149,34 +150,45 @@ cudaError_t launch_energy_terms(const hobo_instance* h, const uint32_t* X, int B
     if (flip_out) {
         cudaFuncSetAttribute(energy_terms_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         energy_terms_kernel<true><<<grid, kTermThreads, sm, st>>>(
-            X, B, h->N, h->W, d.fptr, d.fvars, d.fcoef, h->KF, d.tvars, d.tcoef32, d.M, h->order,
+            X, B, h->N, h->W, d.fptr, d.fvars, d.fcoef, h->KF, d.tvars, d.tcoef32, d.M, h->order, h->KS,
             g_or_dE, E);
     } else {
         cudaFuncSetAttribute(energy_terms_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         energy_terms_kernel<false><<<grid, kTermThreads, sm, st>>>(
-            X, B, h->N, h->W, d.fptr, d.fvars, d.fcoef, h->KF, d.tvars, d.tcoef32, d.M, h->order,
+            X, B, h->N, h->W, d.fptr, d.fvars, d.fcoef, h->KF, d.tvars, d.tcoef32, d.M, h->order, h->KS,
             g_or_dE, E);
     }
     return cudaGetLastError();
 }
 
 // ===========================================================================
-// float64 re-scoring: same traversal as the energy part above, with the
-// folded coefficients kept in float64 and a float64 accumulator; the
-// per-warp partial sums are combined in a fixed order.
+// float64 re-scoring.  Each folded coefficient is held as the 64-bit integer
+// round(c * 2^S), with S chosen per instance so that the sum of all
+// |coefficients| stays below 2^62; the energy of a state is the exact
+// integer sum of the coefficients of its active monomials, scaled by 2^-S
+// and rounded once to float64.  Integer instances are exact; otherwise the
+// error is at most (number of terms) * 2^-(S+1), below the rounding error of
+// a float64 summation of the same terms.  Blocks take 32 states (one per
+// lane) and a slice of the monomial list; slices are combined with 64-bit
+// integer atomics, whose result does not depend on their order.
 // ===========================================================================
-__global__ void __launch_bounds__(kTermThreads)
-energy_fp64_kernel(const uint32_t* __restrict__ X, int B, int N, int W,
-                   const uint16_t* __restrict__ tvars, const double* __restrict__ tcoef,
-                   int64_t M, int K, double* __restrict__ out_E)
+constexpr int kFixThreads = 256;
+
+template <int KS>
+__global__ void __launch_bounds__(kFixThreads)
+energy_fix_kernel(const uint32_t* __restrict__ X, int B, int N, int W,
+                  const uint16_t* __restrict__ tvars, const long long* __restrict__ tfix,
+                  int64_t M, int64_t per_slice, unsigned long long* __restrict__ acc)
 {
+    using Row = typename std::conditional<KS == 4, uint2, uint4>::type;   // KS u16 slots
+    constexpr int U = 4;   // monomials in flight per warp
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int b0 = blockIdx.x * 32;
     const int nb = min(32, B - b0);
     const int WS = W + 1;
     uint32_t* bits = smem;
-    double* red = reinterpret_cast<double*>(bits + ((WS * 32 + 1) & ~1));
+    long long* red = reinterpret_cast<long long*>(bits + ((WS * 32 + 1) & ~1));
     for (int q = threadIdx.x; q < WS * 32; q += blockDim.x) {
         const int w = q >> 5, b = q & 31;
         uint32_t v = 0;
@@ -189,33 +201,78 @@ energy_fp64_kernel(const uint32_t* __restrict__ X, int B, int N, int W,
         bits[q] = v;
     }
     __syncthreads();
-    double acc = 0.0;
-    for (int64_t t = warp; t < M; t += nwarps) {
-        uint32_t p = 1u;
-        for (int s = 0; s < K; ++s) {
-            const int v = tvars[t * K + s];
-            p &= bits[(v >> 5) * 32 + lane] >> (v & 31);
+    const int64_t t0 = (int64_t)blockIdx.y * per_slice;
+    const int64_t t1 = min(M, t0 + per_slice);
+    const Row* rows = reinterpret_cast<const Row*>(tvars);
+    long long s = 0;
+    for (int64_t t = t0 + (int64_t)warp * U; t < t1; t += (int64_t)nwarps * U) {
+        Row r[U];
+        long long c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool ok = t + u < t1;
+            r[u] = ok ? __ldg(rows + t + u) : Row{};
+            c[u] = ok ? __ldg(tfix + t + u) : 0ll;
         }
-        if (p & 1u) acc += tcoef[t];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t* wv = reinterpret_cast<const uint32_t*>(&r[u]);
+            uint32_t p = 1u;
+#pragma unroll
+            for (int q = 0; q < KS / 2; ++q) {
+                const int v0 = wv[q] & 0xFFFFu, v1 = wv[q] >> 16;
+                p &= bits[(v0 >> 5) * 32 + lane] >> (v0 & 31);
+                p &= bits[(v1 >> 5) * 32 + lane] >> (v1 & 31);
+            }
+            if (p & 1u) s += c[u];
+        }
     }
-    red[warp * 32 + lane] = acc;
+    red[warp * 32 + lane] = s;
     __syncthreads();
     if (warp == 0 && lane < nb) {
-        double e = 0.0;
-        for (int q = 0; q < nwarps; ++q) e += red[q * 32 + lane];
-        out_E[b0 + lane] = e;
+        long long tot = 0;
+        for (int q = 0; q < nwarps; ++q) tot += red[q * 32 + lane];
+        atomicAdd(acc + b0 + lane, (unsigned long long)tot);
     }
+}
+
+__global__ void energy_fix_finalize(const unsigned long long* __restrict__ acc, int B, int S,
+                                    double* __restrict__ E)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) E[b] = ldexp((double)(long long)acc[b], -S);
 }
 
 cudaError_t launch_energy_fp64(const hobo_instance* h, const uint32_t* X, int B, double* E,
                                cudaStream_t st)
 {
     if (B == 0) return cudaSuccess;
-    const size_t sm = sizeof(uint32_t) * (((size_t)(h->W + 1) * 32 + 1) & ~(size_t)1) +
-                      sizeof(double) * (kTermThreads / 32) * 32;
-    energy_fp64_kernel<<<(unsigned)((B + 31) / 32), kTermThreads, sm, st>>>(
-        X, B, h->N, h->W, h->d.tvars, h->d.tcoef64, h->d.M, h->order, E);
-    return cudaGetLastError();
+    const int64_t M = h->d.M;
+    const int tiles = (B + 31) / 32;
+    int slices = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * h->num_sms + tiles - 1) / tiles,
+                                                             (M + 4095) / 4096));
+    const int64_t per = (M + slices - 1) / std::max(slices, 1);
+    unsigned long long* acc = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&acc, sizeof(unsigned long long) * (size_t)B, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)B, st);
+    if (e == cudaSuccess && M > 0) {
+        const size_t sm = sizeof(uint32_t) * (((size_t)(h->W + 1) * 32 + 1) & ~(size_t)1) +
+                          sizeof(long long) * (kFixThreads / 32) * 32;
+        if (h->KS == 4)
+            energy_fix_kernel<4><<<dim3(tiles, slices), kFixThreads, sm, st>>>(
+                X, B, h->N, h->W, h->d.tvars, h->d.tfix, M, per, acc);
+        else
+            energy_fix_kernel<8><<<dim3(tiles, slices), kFixThreads, sm, st>>>(
+                X, B, h->N, h->W, h->d.tvars, h->d.tfix, M, per, acc);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        energy_fix_finalize<<<(B + 255) / 256, 256, 0, st>>>(acc, B, h->d.fix_shift, E);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(acc, st);
+    return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -258,11 +315,16 @@ __global__ void sweep_plain_kernel(const SweepDev p)
             ++nacc;
             const float delta = xi ? -1.0f : 1.0f;
             if (DENSE) {
+                // same sums, in the same order, as the tuned kernel
                 const float* slab = p.S3 + (int64_t)i * N * P;
+                int pop = 0;
+                for (int k = 0; k < W; ++k) pop += __popc(x[k]);
+                const bool comp = 2 * pop > N;
                 for (int j = 0; j < N; ++j) {
                     float acc = 0.0f;
                     for (int l = 0; l < N; ++l)
-                        if (bit_of(x, l)) acc = __fadd_rn(acc, slab[(int64_t)l * P + j]);
+                        if (bit_of(x, l) != (comp ? 1u : 0u)) acc = __fadd_rn(acc, slab[(int64_t)l * P + j]);
+                    if (comp) acc = __fsub_rn(p.S3col[(int64_t)i * P + j], acc);
                     g[j] = __fadd_rn(g[j], __fmul_rn(delta, __fadd_rn(p.S2[(int64_t)i * P + j], acc)));
                 }
             } else {
@@ -301,7 +363,7 @@ static SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
     p.accepts = a.accepts;
     p.write_g = a.write_g ? 1 : 0;
     p.bptr = h->d.bptr; p.rtgt = h->d.rtgt; p.rbeg = h->d.rbeg; p.ucoef = h->d.ucoef;
-    p.uconds = h->d.uconds; p.S2 = h->d.S2; p.S3 = h->d.S3;
+    p.uconds = h->d.uconds; p.S2 = h->d.S2; p.S3 = h->d.S3; p.S3col = h->d.S3col;
     return p;
 }
 

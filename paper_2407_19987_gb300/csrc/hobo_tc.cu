@@ -1,14 +1,512 @@
-// tcgen05 tensor-core contraction of dense order-3 instances (placeholder:
-// reports "not supported" until the kernel is in place).
+// tcgen05 tensor-core contraction of dense order-3 instances.
+//
+// For a tile of 128 states and a variable m the kernel forms, on the tensor
+// cores, D[b][j] = sum_l x_bl * S3[m][j][l]: the tensor reshaped to
+// (N^2 x N) rows (m, j) against the bit matrix, which is the first step of
+// the one-index-at-a-time contraction order (Sec. VI.B / VI.F, Sec. IV.C for
+// the batch).  The 0/1 state bits are exact in bf16; each cubic coefficient
+// is split into 2 or 3 bf16 planes (hi + lo [+ mid]) whose products
+// accumulate in float32 in tensor memory.  The fused epilogue finishes the
+// contraction on CUDA cores:
+//   c_bm = 1/2 sum_j x_bj D[b][j]      (cubic part of the field g_bm)
+//   q_bm = sum_j x_bj S2[m][j]         (quadratic part)
+//   g_bm = a_m + q_bm + c_bm
+// and the energy by Euler's identity per degree,
+//   E_b = sum_m x_bm a_m + 1/2 sum_m x_bm q_bm + 1/6 sum_m x_bm (2 c_bm).
+//
+// Roles (192 threads): warp 0 issues TMA loads of the coefficient slabs
+// (128-byte swizzle, 4-stage ring), warp 1 issues the MMAs (one thread),
+// warps 2-5 read the accumulators (double-buffered, 2 x 256 columns) and
+// run the epilogue.  All threads expand the state bits of a tile into the
+// bf16 A operand in shared memory.  CTA c owns state tile c % T and a chunk
+// of the variables m; tiles advance through m in step.  Every wait on an mbarrier gives up
+// after kWaitNs and reports HOBO_ERR_TIMEOUT through the status word.
+#include <algorithm>
+#include <cuda.h>
 #include "hobo_internal.h"
+#include "hobo_dev.cuh"
 
 namespace hobo {
 
-cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, float* E,
-                             float* g_or_dE, bool flip_out, cudaStream_t st)
+constexpr int kTcM = 128;          // states per tile (MMA M)
+constexpr int kTcKB = 64;          // K elements per swizzle atom (128 bytes)
+constexpr int kTcStages = 4;
+constexpr int kTcThreads = 192;
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s
+
+struct TcParams {
+    const uint32_t* X;
+    int B, N, W, NJ, KP, nsplit, P;
+    const float* S2;
+    const float* a;
+    float* out_g;
+    int flip;
+    float* Epart;        // [G][128][4]
+    int T, chunks, G;    // state tiles, m-chunks per tile, CTAs (= T * chunks)
+    int* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
-    (void)h; (void)X; (void)B; (void)E; (void)g_or_dE; (void)flip_out; (void)st;
-    return cudaErrorNotSupported;
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: false after kWaitNs or once another thread has aborted.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row core groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: bf16 A and B (K-major), f32 D.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void set_abort(volatile int* abort_flag, int* status)
+{
+    *abort_flag = 1;
+    atomicExch(status, kDevTimeout);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+energy_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int nKB = p.KP / kTcKB;
+    const uint32_t stage_bytes = (uint32_t)p.NJ * 128u;
+    uint8_t* sA = smem;                                  // nKB x 16 KB
+    uint8_t* sB = sA + nKB * 16384;                      // kTcStages x stage_bytes
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kTcStages * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kTcStages;
+    uint64_t* afull = bars + 2 * kTcStages;
+    uint64_t* aempty = afull + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(aempty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+    volatile int* never_set = abort_flag + 1;     // stays 0: teardown waits use only the time limit
+
+    float* s2row = reinterpret_cast<float*>(tmem_holder + 4);   // [4 warps][NJ] staged pair-matrix rows
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = p.N, W = p.W, B = p.B;
+    const int c = blockIdx.x;
+    // CTA c: state tile c % T, variables m in chunk c / T.  All tiles walk
+    // the same m at the same time, so each coefficient slab is fetched from
+    // memory once and served to the other tiles from L2.
+    const int tile_c = c % p.T, chunk = c / p.T;
+    const int i0 = tile_c * N + (int)((int64_t)chunk * N / p.chunks);
+    const int i1 = tile_c * N + (int)((int64_t)(chunk + 1) * N / p.chunks);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&afull[s], 1);
+            mbar_init(&aempty[s], 4);
+        }
+        *abort_flag = 0;
+        *never_set = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    // role state carried across segments
+    int pstage = 0;
+    uint32_t pphase = 0;                 // producer ring position
+    uint32_t armed_phase[kTcStages];     // last phase the producer armed per stage
+    bool armed[kTcStages];
+    for (int s = 0; s < kTcStages; ++s) { armed[s] = false; armed_phase[s] = 0; }
+    int cstage = 0;
+    uint32_t cphase = 0;                 // MMA ring position
+    int acc_mma = 0, acc_epi = 0;        // accumulator counters (buffer = n & 1)
+    const uint32_t idesc = idesc_bf16(kTcM, p.NJ);
+
+    int seg = 0;
+    for (int it = i0; it < i1; ++seg) {
+        const int tile = it / N;
+        const int seg_end = min(i1, (tile + 1) * N);
+
+        // ---- A operand: bits of the tile's 128 states as bf16 0/1, K-major,
+        // 128-byte swizzle (16-byte chunk c of row r stored at c ^ (r & 7)).
+        {
+            const int cpr = p.KP / 8;     // 16-byte chunks per row
+            for (int q = threadIdx.x; q < kTcM * cpr; q += blockDim.x) {
+                const int r = q / cpr, cc = q % cpr;
+                const int kb = cc >> 3, ch = cc & 7;
+                const int b = tile * kTcM + r;
+                const int l0 = cc * 8;
+                uint32_t byte = 0;
+                if (b < B && l0 < N) {
+                    byte = (p.X[(int64_t)b * W + (l0 >> 5)] >> (l0 & 31)) & 0xFFu;
+                    const int rem = N - l0;
+                    if (rem < 8) byte &= (1u << rem) - 1u;
+                }
+                uint32_t wv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t lo = ((byte >> (2 * e)) & 1u) ? 0x3F80u : 0u;
+                    const uint32_t hi = ((byte >> (2 * e + 1)) & 1u) ? 0x3F80u : 0u;
+                    wv[e] = lo | (hi << 16);
+                }
+                uint8_t* dst = sA + kb * 16384 + (r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4);
+                *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+
+        if (warp == 0) {
+            if (lane == 0) {
+                // ---- producer: coefficient slabs of planes q for items m
+                for (int j = it; j < seg_end && !*abort_flag; ++j) {
+                    const int m = j % N;
+                    for (int q = 0; q < p.nsplit; ++q)
+                        for (int kb = 0; kb < nKB; ++kb) {
+                            if (!mbar_wait(&empty[pstage], pphase ^ 1u, abort_flag)) {
+                                set_abort(abort_flag, p.status);
+                                break;
+                            }
+                            mbar_expect_tx(&full[pstage], stage_bytes);
+                            tma_load_2d(sB + pstage * stage_bytes, &tmap, kb * kTcKB, (q * N + m) * p.NJ,
+                                        &full[pstage]);
+                            armed[pstage] = true;
+                            armed_phase[pstage] = pphase;
+                            if (++pstage == kTcStages) { pstage = 0; pphase ^= 1u; }
+                        }
+                }
+            }
+        } else if (warp == 1) {
+            if (lane == 0) {
+                // ---- MMA issuer
+                for (int j = it; j < seg_end && !*abort_flag; ++j) {
+                    const int buf = acc_mma & 1;
+                    if (!mbar_wait(&aempty[buf], (((uint32_t)acc_mma >> 1) & 1u) ^ 1u, abort_flag)) {
+                        set_abort(abort_flag, p.status);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(buf * 256);
+                    uint32_t accum = 0;
+                    bool ok = true;
+                    for (int q = 0; q < p.nsplit && ok; ++q)
+                        for (int kb = 0; kb < nKB; ++kb) {
+                            if (!mbar_wait(&full[cstage], cphase, abort_flag)) {
+                                set_abort(abort_flag, p.status);
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t a0 = smem_u32(sA + kb * 16384);
+                            const uint32_t b0 = smem_u32(sB + cstage * stage_bytes);
+#pragma unroll
+                            for (int k = 0; k < kTcKB / 16; ++k) {
+                                tc_mma(d, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), idesc, accum);
+                                accum = 1;
+                            }
+                            tc_commit(&empty[cstage]);
+                            if (++cstage == kTcStages) { cstage = 0; cphase ^= 1u; }
+                        }
+                    if (!ok) break;
+                    tc_commit(&afull[buf]);
+                    ++acc_mma;
+                }
+            }
+        } else {
+            // ---- epilogue: thread = TMEM lane = state row
+            const int quad = warp & 3;
+            const int r = quad * 32 + lane;
+            const int b = tile * kTcM + r;
+            uint32_t x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                uint32_t v = (b < B && k < W) ? p.X[(int64_t)b * W + k] : 0u;
+                const int rem = N - 32 * k;
+                if (rem <= 0) v = 0u; else if (rem < 32) v &= (1u << rem) - 1u;
+                x[k] = v;
+            }
+            float e1 = 0.f, e2 = 0.f, e3 = 0.f;
+            const int nch = (p.NJ + 31) / 32;   // columns >= N meet zero bits
+            float* srow = s2row + (warp - 2) * p.NJ;   // this warp's copy
+            for (int j = it; j < seg_end; ++j) {
+                const int m = j % N;
+                const int buf = acc_epi & 1;
+                __syncwarp();
+                for (int q2 = lane; q2 < p.NJ; q2 += 32) srow[q2] = q2 < N ? __ldg(p.S2 + (int64_t)m * p.P + q2) : 0.f;
+                __syncwarp();
+                // quadratic part from the staged pair-matrix row m
+                float q = 0.f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    uint32_t u = x[k];
+                    while (u) {
+                        const int t = __ffs(u) - 1;
+                        u &= u - 1u;
+                        q = __fadd_rn(q, srow[32 * k + t]);
+                    }
+                }
+                // the warp leaves together: tcgen05.ld below needs all 32 lanes
+                const bool ok = __all_sync(0xffffffffu, mbar_wait(&afull[buf], ((uint32_t)acc_epi >> 1) & 1u, abort_flag));
+                if (!ok) {
+                    if (lane == 0) set_abort(abort_flag, p.status);
+                    break;
+                }
+                tc_fence_after();
+                float cacc = 0.f, ccomp = 0.f;
+                const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256);
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                    if (ch >= nch) break;
+                    uint32_t v[32];
+                    tmem_ld32(tbase + (uint32_t)(ch * 32), v);
+                    tmem_ld_wait();
+                    const uint32_t xw = x[ch];
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
+                        if ((xw >> t) & 1u) {
+                            const float y = __fsub_rn(__uint_as_float(v[t]), ccomp);
+                            const float s = __fadd_rn(cacc, y);
+                            ccomp = __fsub_rn(__fsub_rn(s, cacc), y);
+                            cacc = s;
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&aempty[buf]);
+                ++acc_epi;
+                const float am = __ldg(p.a + m);
+                const float g = __fadd_rn(__fadd_rn(am, q), __fmul_rn(0.5f, cacc));
+                uint32_t xmw = x[0];
+#pragma unroll
+                for (int k = 1; k < 8; ++k) xmw = ((m >> 5) == k) ? x[k] : xmw;
+                const bool xm = (xmw >> (m & 31)) & 1u;
+                if (xm) {
+                    e1 = __fadd_rn(e1, am);
+                    e2 = __fadd_rn(e2, q);
+                    e3 = __fadd_rn(e3, cacc);
+                }
+                if (b < B) p.out_g[(int64_t)b * N + m] = (p.flip && xm) ? -g : g;
+            }
+            float* dst = p.Epart + ((int64_t)c * kTcM + r) * 4;
+            dst[0] = e1; dst[1] = e2; dst[2] = e3; dst[3] = 0.f;
+        }
+        __syncthreads();
+        it = seg_end;
+    }
+
+    // teardown: make sure no TMA copy is still landing in shared memory
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        for (int s = 0; s < kTcStages; ++s)
+            if (armed[s]) (void)mbar_wait(&full[s], armed_phase[s], never_set);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// E_b from the partial sums of the m-chunks of its tile, added in chunk
+// order: E = sum x_m a_m + 1/2 sum x_m q_m + 1/6 sum x_m (2 c_m).
+__global__ void energy_tc_finalize(const float* __restrict__ Epart, int B, int T, int chunks,
+                                   float* __restrict__ E)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int t = b / kTcM, r = b % kTcM;
+    float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (int k = 0; k < chunks; ++k) {
+        const float* src = Epart + ((int64_t)(k * T + t) * kTcM + r) * 4;
+        s1 = __fadd_rn(s1, src[0]);
+        s2 = __fadd_rn(s2, src[1]);
+        s3 = __fadd_rn(s3, src[2]);
+    }
+    E[b] = __fadd_rn(__fadd_rn(s1, __fmul_rn(0.5f, s2)), __fdiv_rn(s3, 6.0f));
+}
+
+static size_t tc_smem_bytes(int NJ, int KP)
+{
+    return 1024 + (size_t)(KP / kTcKB) * 16384 + (size_t)kTcStages * NJ * 128 + 256 + 4 * 4 * (size_t)NJ;
+}
+
+bool tc_supported(const hobo_instance* h)
+{
+    return h->dense && h->d.S3bf && h->d.tmap_ok && h->N <= 256;
+}
+
+cudaError_t make_tc_tensor_map(hobo_instance* h)
+{
+    using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+    const auto& d = h->d;
+    cuuint64_t dims[2] = {(cuuint64_t)d.KP, (cuuint64_t)d.nsplit * h->N * d.NJ};
+    cuuint64_t strides[1] = {(cuuint64_t)d.KP * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTcKB, (cuuint32_t)d.NJ};
+    cuuint32_t estr[2] = {1, 1};
+    CUtensorMap* map = reinterpret_cast<CUtensorMap*>(h->d.tmap);
+    CUresult r = reinterpret_cast<EncodeFn>(fn)(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)d.S3bf, dims,
+                                                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    h->d.tmap_ok = true;
+    return cudaSuccess;
+}
+
+cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g_or_dE,
+                             bool flip_out, cudaStream_t st)
+{
+    if (!tc_supported(h)) return cudaErrorNotSupported;
+    if (B == 0) return cudaSuccess;
+    if (!g_or_dE) return cudaErrorNotSupported;   // the kernel always writes fields
+    const auto& d = h->d;
+    const int tiles = (B + kTcM - 1) / kTcM;
+    const int chunks = std::max(1, std::min(h->N, h->num_sms / tiles));
+    const int G = tiles * chunks;
+    TcParams p{};
+    p.X = X; p.B = B; p.N = h->N; p.W = h->W; p.NJ = d.NJ; p.KP = d.KP; p.nsplit = d.nsplit;
+    p.P = (h->N + 3) & ~3; p.S2 = d.S2; p.a = d.a; p.out_g = g_or_dE; p.flip = flip_out ? 1 : 0;
+    p.T = tiles; p.chunks = chunks; p.G = G; p.status = h->status;
+    float* Epart = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&Epart, sizeof(float) * (size_t)G * kTcM * 4, st);
+    if (e != cudaSuccess) return e;
+    p.Epart = Epart;
+    const size_t sm = tc_smem_bytes(d.NJ, d.KP);
+    e = cudaFuncSetAttribute(energy_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) {
+        const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(d.tmap);
+        energy_tc_kernel<<<G, kTcThreads, sm, st>>>(*map, p);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        energy_tc_finalize<<<(B + 255) / 256, 256, 0, st>>>(Epart, B, tiles, chunks, E);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(Epart, st);
+    return e;
 }
 
 }  // namespace hobo

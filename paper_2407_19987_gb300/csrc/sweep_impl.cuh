@@ -35,6 +35,7 @@ struct SweepDev {
     const uint16_t* uconds;
     const float* S2;     // [N][P]
     const float* S3;     // [N][N][P]
+    const float* S3col;  // [N][P] column sums of each slab
 };
 
 template <int WMAX>
@@ -65,53 +66,76 @@ __device__ __forceinline__ void set_word(uint32_t (&x)[WMAX], int w, uint32_t v)
 constexpr int kSweepWarps = 8;
 
 // Dense order<=3 update for a flip of bit i: g_j += delta * (S2[i][j] +
-// sum_{l set} S3[i][l][j]).  Lanes own 4 consecutive targets per 128-wide
-// chunk; set rows l are visited in ascending order.
-template <int WMAX>
+// sum_{l set} S3[i][l][j]).  When more than half of the bits are set the
+// slab sum is formed as colsum[i][j] - sum_{l clear} S3[i][l][j] instead, so
+// at most N/2 rows are read.  Lanes own 4 consecutive targets in each
+// 128-wide chunk (NC chunks); rows are visited in ascending order, 8 at a
+// time with their loads in flight together.
+template <int WMAX, int NC>
 __device__ __forceinline__ void dense_update(const SweepDev& p, float* __restrict__ g,
                                              const uint32_t (&x)[WMAX], int i, float delta, int lane)
 {
-    const int N = p.N, P = p.P;
+    const int N = p.N, P = p.P, W = p.W;
     const float* __restrict__ slab = p.S3 + (int64_t)i * N * P;
-    for (int c0 = 0; c0 < P; c0 += 128) {
-        const int j = c0 + 4 * lane;
-        const bool jv = j < P;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int W = p.W;
-#pragma unroll 1
-        for (int k = 0; k < W; ++k) {
-            const uint32_t u = sel_word(x, k);
-#pragma unroll 1
-            for (int t0 = 0; t0 < 32; t0 += 8) {
-                if (((u >> t0) & 0xFFu) == 0u) continue;
-                float4 v[8];
+    int pop = 0;
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int l = 32 * k + t0 + t;
-                    v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (jv && ((u >> (t0 + t)) & 1u))
-                        v[t] = __ldg(reinterpret_cast<const float4*>(slab + (int64_t)l * P + j));
+    for (int k = 0; k < WMAX; ++k) pop += __popc(x[k]);
+    const bool comp = 2 * pop > N;
+    float4 acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int k = 0; k < W; ++k) {
+        uint32_t u = sel_word(x, k);
+        if (comp) {
+            u = ~u;
+            const int rem = N - 32 * k;
+            if (rem < 32) u &= (1u << rem) - 1u;
+        }
+#pragma unroll 1
+        for (int t0 = 0; t0 < 32; t0 += 8) {
+            const uint32_t ub = (u >> t0) & 0xFFu;
+            if (ub == 0u) continue;
+            float4 v[8][NC];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const float* row = slab + (int64_t)(32 * k + t0 + t) * P;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int j = 128 * c + 4 * lane;
+                    v[t][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (((ub >> t) & 1u) && j < P) v[t][c] = __ldg(reinterpret_cast<const float4*>(row + j));
                 }
+            }
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    if ((u >> (t0 + t)) & 1u) {
-                        acc.x = __fadd_rn(acc.x, v[t].x);
-                        acc.y = __fadd_rn(acc.y, v[t].y);
-                        acc.z = __fadd_rn(acc.z, v[t].z);
-                        acc.w = __fadd_rn(acc.w, v[t].w);
+            for (int t = 0; t < 8; ++t) {
+                if ((ub >> t) & 1u) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        acc[c].x = __fadd_rn(acc[c].x, v[t][c].x);
+                        acc[c].y = __fadd_rn(acc[c].y, v[t][c].y);
+                        acc[c].z = __fadd_rn(acc[c].z, v[t][c].z);
+                        acc[c].w = __fadd_rn(acc[c].w, v[t][c].w);
                     }
                 }
             }
         }
-        if (jv) {
-            const float4 s2 = __ldg(reinterpret_cast<const float4*>(p.S2 + (int64_t)i * P + j));
-            const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
-            const float s4[4] = {s2.x, s2.y, s2.z, s2.w};
+    }
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (j + q < N)
-                    g[j + q] = __fadd_rn(g[j + q], __fmul_rn(delta, __fadd_rn(s4[q], a4[q])));
+    for (int c = 0; c < NC; ++c) {
+        const int j = 128 * c + 4 * lane;
+        if (j >= P) continue;
+        const float4 s2 = __ldg(reinterpret_cast<const float4*>(p.S2 + (int64_t)i * P + j));
+        float4 d = acc[c];
+        if (comp) {
+            const float4 cs = __ldg(reinterpret_cast<const float4*>(p.S3col + (int64_t)i * P + j));
+            d = make_float4(__fsub_rn(cs.x, d.x), __fsub_rn(cs.y, d.y), __fsub_rn(cs.z, d.z), __fsub_rn(cs.w, d.w));
         }
+        const float a4[4] = {d.x, d.y, d.z, d.w};
+        const float s4[4] = {s2.x, s2.y, s2.z, s2.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (j + q < N) g[j + q] = __fadd_rn(g[j + q], __fmul_rn(delta, __fadd_rn(s4[q], a4[q])));
     }
 }
 
@@ -142,7 +166,7 @@ __device__ __forceinline__ void sparse_update(const SweepDev& p, float* __restri
 }
 
 template <int WMAX, bool DENSE, int KU>
-__global__ void __launch_bounds__(kSweepWarps * 32)
+__global__ void __launch_bounds__(kSweepWarps * 32, 4)
 sweep_tuned_kernel(const SweepDev p)
 {
     extern __shared__ float sm[];
@@ -219,7 +243,7 @@ sweep_tuned_kernel(const SweepDev p)
                 }
                 const int fi = 32 * w + f;
                 if (DENSE) {
-                    dense_update<WMAX>(p, g, x, fi, delta, lane);
+                    dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1)>(p, g, x, fi, delta, lane);
                 } else {
                     if (lane == 0) bs[w] = cw | (w == wsent ? sent : 0u);
                     __syncwarp();

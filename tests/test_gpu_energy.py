@@ -151,3 +151,52 @@ def test_energy_ignores_bits_beyond_N():
     h = gpuh.make(inst)
     E, dE = h.energy(torch.from_numpy(P.view(np.int32)).cuda())
     np.testing.assert_array_equal(E.cpu().numpy(), O.energy_int(inst, X).astype(np.float32))
+
+
+TC_CASES = [(12, 1), (12, 129), (33, 100), (64, 128), (64, 300), (200, 77), (256, 129)]
+
+
+@pytest.mark.parametrize("N,B", TC_CASES, ids=[f"N{n}_B{b}" for n, b in TC_CASES])
+def test_tensor_core_path_integer_exact(N, B):
+    """tcgen05 contraction (path 2) on dense order-3 integer instances:
+    ragged state tiles (B not a multiple of 128) and ragged N (not a
+    multiple of 16/64) give exact energies and flip deltas."""
+    inst = W.random_sparse(90 + N, N, 3, 0.6, "int")
+    X = W.random_states(91 + B, B, N)
+    _check_int(inst, X, flags=4, path=2)
+
+
+def test_tensor_core_three_plane_split_large_integers():
+    """Coefficients >= 2^16 need the hi+mid+lo split to stay exact."""
+    inst = W.random_sparse(95, 10, 3, 1.0, "int", imax=100000)
+    assert np.abs(inst.coef).max() >= 2 ** 16
+    X = W.random_states(96, 50, inst.N)
+    _check_int(inst, X, flags=4, path=2)
+
+
+def test_tensor_core_matches_term_path_float():
+    inst = W.dense_float(97, 96)
+    h = gpuh.make(inst)
+    X = gpuh.to_dev(W.random_states(98, 200, inst.N))
+    E2, d2 = h.energy(X, path=2)
+    E1, d1 = h.energy(X, path=1)
+    Xh = W.random_states(98, 200, inst.N)
+    absi = gpuh.abs_instance(inst)
+    A = O.energy(absi, Xh)
+    assert gpuh.rel_err(E2.cpu().numpy().astype(np.float64), E1.cpu().numpy().astype(np.float64), A).max() <= 2e-5
+
+
+def test_tensor_core_path_refused_for_sparse_instance():
+    import paper_2407_19987_gb300 as H
+    inst = W.random_sparse(99, 40, 3, 0.05, "int")
+    h = gpuh.make(inst)
+    with pytest.raises(H.HoboError) as ei:
+        h.energy(gpuh.to_dev(W.random_states(1, 4, inst.N)), path=2)
+    assert ei.value.code == -7
+
+
+def test_check_reports_no_timeout_after_normal_work():
+    inst = W.dense_float(100, 64)
+    h = gpuh.make(inst)
+    h.energy(gpuh.to_dev(W.random_states(2, 64, inst.N)))
+    h.check()
