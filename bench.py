@@ -198,7 +198,7 @@ def run_ours(a):
 
     def step(events=None, accepts=False):
         return h.anneal(seed, B, betas, mode=mode, bestX=bestX, bestE32=bestE32,
-                        want_accepts=accepts, sweep_events=events)
+                        want_accepts=accepts, want_bytes=accepts, sweep_events=events)
 
     for _ in range(a.warmup):
         step()
@@ -207,6 +207,7 @@ def run_ours(a):
     r = step(accepts=True)
     torch.cuda.synchronize()
     accepts = int(r["accepts"].sum().item())
+    coef_bytes = int(r["coef_bytes"].sum().item())
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
@@ -255,10 +256,11 @@ def run_ours(a):
     d2h = hX.numel() * 4 + hE.numel() * 8
 
     pk, pk_kind = peaks()
-    # dense sweep: each accepted flip of bit i reads the set rows of the
-    # (N x P) float32 slab S3[i] (about N/2 rows) plus the S2 row.
-    P = (inst.N + 3) & ~3
-    bytes_sweep = accepts * (inst.N / 2 + 1) * P * 4 + B * (inst.N * 4 + 2 * W_ * 4 * 2 + 16)
+    # sweep kernel: coefficient bytes it read for the accepted flips (counted
+    # by the kernel: min(set, clear) rows of the float32 slab of the flipped
+    # bit, plus its pair row and column-sum row) and the per-state data it
+    # loads and stores once (fields, bits, energies).
+    bytes_sweep = coef_bytes + B * (inst.N * 4 + 4 * W_ * 4 + 16)
     achieved = bytes_sweep / (sweep_avg / 1000.0) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -268,7 +270,8 @@ def run_ours(a):
                                f"B={B} states per GPU, {S} sweeps, geometric T 10->0.01",
                    "mode": a.mode, "dense_layout": info["dense"], "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": f"replicas x{world} (independent states per GPU)",
-                   "accepted_flips_per_step": accepts, "sweep_kernel_ms": sweep_avg},
+                   "accepted_flips_per_step": accepts, "sweep_coef_bytes_per_step": coef_bytes,
+                   "sweep_kernel_ms": sweep_avg},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": None,
                      "kernel": "sweep_tuned_kernel (dense)", "peak_kind": pk_kind},

@@ -168,6 +168,9 @@ typedef struct {
                               float instance; without them fields and
                               energies are recomputed from X_io) */
     int64_t* accepts;      /* device [B] or NULL: accepted flips (added to) */
+    int64_t* coef_bytes;   /* device [B] or NULL: bytes of coefficient data the
+                              sweep read to update each state's fields after
+                              its accepted flips (added to) */
     void* ev_sweep_begin;  /* cudaEvent_t or NULL: recorded on `stream` right
                               before the sweep kernel is enqueued */
     void* ev_sweep_end;    /* cudaEvent_t or NULL: recorded right after it */

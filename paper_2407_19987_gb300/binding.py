@@ -53,7 +53,7 @@ class hobo_info_t(C.Structure):
 class hobo_anneal_opts(C.Structure):
     _fields_ = [("mode", C.c_int), ("states_per_block", C.c_int), ("sweep0", C.c_int),
                 ("resume", C.c_int), ("X_io", C.c_void_p), ("bestE32_io", C.c_void_p),
-                ("E_io", C.c_void_p), ("g_io", C.c_void_p), ("accepts", C.c_void_p), ("ev_sweep_begin", C.c_void_p),
+                ("E_io", C.c_void_p), ("g_io", C.c_void_p), ("accepts", C.c_void_p), ("coef_bytes", C.c_void_p), ("ev_sweep_begin", C.c_void_p),
                 ("ev_sweep_end", C.c_void_p)]
 
 
@@ -187,8 +187,8 @@ class Instance:
     def anneal(self, seed: int, B: int, betas: np.ndarray, *, mode: int = HOBO_ANNEAL_TUNED,
                states_per_block: int = 0, sweep0: int = 0, resume: bool = False, X=None,
                bestX=None, bestE32=None, E=None, g=None, want_final: bool = False,
-               want_fields: bool = False, want_accepts: bool = False, device=None, stream=None,
-               sweep_events=None) -> dict:
+               want_fields: bool = False, want_accepts: bool = False, want_bytes: bool = False,
+               device=None, stream=None, sweep_events=None) -> dict:
         """Batched annealing (hobo_anneal).  betas: host float32 [sweeps].
         Returns a dict of CUDA tensors: bestX [B, W] int32, bestE [B] f64, and
         when asked X (final), E (final f32), bestE32, accepts."""
@@ -207,6 +207,7 @@ class Instance:
         if g is None and want_fields:
             g = torch.empty((B, self.N), dtype=torch.float32, device=dev)
         acc = torch.zeros(B, dtype=torch.int64, device=dev) if want_accepts else None
+        cb = torch.zeros(B, dtype=torch.int64, device=dev) if want_bytes else None
         ev0 = ev1 = None
         if sweep_events is not None:
             for e in sweep_events:          # torch creates its events lazily
@@ -214,7 +215,7 @@ class Instance:
                     e.record()
             ev0, ev1 = sweep_events[0].cuda_event, sweep_events[1].cuda_event
         o = hobo_anneal_opts(mode, states_per_block, sweep0, 1 if resume else 0,
-                             _ptr(X), _ptr(bestE32), _ptr(E), _ptr(g), _ptr(acc), ev0, ev1)
+                             _ptr(X), _ptr(bestE32), _ptr(E), _ptr(g), _ptr(acc), _ptr(cb), ev0, ev1)
         _check(load_library().hobo_anneal(self._h, C.c_uint64(seed & (2 ** 64 - 1)), B,
                                           betas.ctypes.data_as(C.c_void_p), betas.shape[0],
                                           _ptr(bestX), _ptr(bestE), C.byref(o), _stream(stream)))
@@ -227,6 +228,8 @@ class Instance:
             out["g"] = g
         if acc is not None:
             out["accepts"] = acc
+        if cb is not None:
+            out["coef_bytes"] = cb
         return out
 
 

@@ -594,6 +594,7 @@ int hobo_anneal(hobo_h h, uint64_t seed, int B, const float* beta, int sweeps, u
     a.S = o.states_per_block;
     a.beta = d_beta; a.X = d_X; a.g = d_g; a.E = d_E; a.bestX = bestX; a.bestE = d_bE;
     a.accepts = o.accepts;
+    a.coef_bytes = o.coef_bytes;
     a.write_g = o.g_io != nullptr;
     if (sweeps > 0) {
         if (o.ev_sweep_begin) ACHECK(cudaEventRecord((cudaEvent_t)o.ev_sweep_begin, st), "event record");

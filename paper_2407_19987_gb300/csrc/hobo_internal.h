@@ -89,6 +89,7 @@ struct SweepArgs {
     uint32_t* bestX = nullptr;     // device [B][W]
     float* bestE = nullptr;        // device [B]
     int64_t* accepts = nullptr;    // device [B] or null
+    int64_t* coef_bytes = nullptr; // device [B] or null
     bool write_g = false;          // tuned: write the final fields back to g
 };
 

@@ -299,6 +299,7 @@ __global__ void sweep_plain_kernel(const SweepDev p)
         for (int k = 0; k < W; ++k) bx[k] = x[k];
     }
     long long nacc = 0;
+    int64_t nbytes = 0;
     u32x4 r = {0u, 0u, 0u, 0u};
     for (int s = 0; s < p.sweeps; ++s) {
         const float beta = p.beta[s];
@@ -320,6 +321,7 @@ __global__ void sweep_plain_kernel(const SweepDev p)
                 int pop = 0;
                 for (int k = 0; k < W; ++k) pop += __popc(x[k]);
                 const bool comp = 2 * pop > N;
+                nbytes += (int64_t)(comp ? N - pop : pop) * P * 4 + (comp ? 2 : 1) * (int64_t)P * 4;
                 for (int j = 0; j < N; ++j) {
                     float acc = 0.0f;
                     for (int l = 0; l < N; ++l)
@@ -328,6 +330,8 @@ __global__ void sweep_plain_kernel(const SweepDev p)
                     g[j] = __fadd_rn(g[j], __fmul_rn(delta, __fadd_rn(p.S2[(int64_t)i * P + j], acc)));
                 }
             } else {
+                nbytes += (int64_t)(p.bptr[i + 1] - p.bptr[i]) * 12 +
+                          (int64_t)(p.rbeg[p.bptr[i + 1]] - p.rbeg[p.bptr[i]]) * (4 + 2 * KU);
                 for (int rr = p.bptr[i]; rr < p.bptr[i + 1]; ++rr) {
                     float acc = 0.0f;
                     for (int e = p.rbeg[rr]; e < p.rbeg[rr + 1]; ++e) {
@@ -351,6 +355,7 @@ __global__ void sweep_plain_kernel(const SweepDev p)
     p.E[b] = E;
     p.bestE[b] = Eb;
     if (p.accepts) p.accepts[b] += nacc;
+    if (p.coef_bytes) p.coef_bytes[b] += nbytes;
 }
 
 static SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
@@ -361,6 +366,7 @@ static SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
     p.k0 = (uint32_t)a.seed; p.k1 = (uint32_t)(a.seed >> 32);
     p.beta = a.beta; p.X = a.X; p.g = a.g; p.E = a.E; p.bestX = a.bestX; p.bestE = a.bestE;
     p.accepts = a.accepts;
+    p.coef_bytes = a.coef_bytes;
     p.write_g = a.write_g ? 1 : 0;
     p.bptr = h->d.bptr; p.rtgt = h->d.rtgt; p.rbeg = h->d.rbeg; p.ucoef = h->d.ucoef;
     p.uconds = h->d.uconds; p.S2 = h->d.S2; p.S3 = h->d.S3; p.S3col = h->d.S3col;

@@ -343,24 +343,32 @@ energy_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams p)
             }
             float e1 = 0.f, e2 = 0.f, e3 = 0.f;
             const int nch = (p.NJ + 31) / 32;   // columns >= N meet zero bits
-            float* srow = s2row + (warp - 2) * p.NJ;   // this warp's copy
+            const int SP = (p.NJ + 31) & ~31;          // staged row pitch, zero padded
+            float* srow = s2row + (warp - 2) * SP;       // this warp's copy
             for (int j = it; j < seg_end; ++j) {
                 const int m = j % N;
                 const int buf = acc_epi & 1;
                 __syncwarp();
-                for (int q2 = lane; q2 < p.NJ; q2 += 32) srow[q2] = q2 < N ? __ldg(p.S2 + (int64_t)m * p.P + q2) : 0.f;
+                for (int q2 = lane; q2 < SP; q2 += 32) srow[q2] = q2 < N ? __ldg(p.S2 + (int64_t)m * p.P + q2) : 0.f;
                 __syncwarp();
-                // quadratic part from the staged pair-matrix row m
-                float q = 0.f;
+                // quadratic part: sum of the staged row m over set bits, four
+                // independent partial sums (x * v with x in {0,1} is exact)
+                float q0 = 0.f, q1 = 0.f, q2s = 0.f, q3 = 0.f;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    uint32_t u = x[k];
-                    while (u) {
-                        const int t = __ffs(u) - 1;
-                        u &= u - 1u;
-                        q = __fadd_rn(q, srow[32 * k + t]);
+                    if (32 * k >= SP) break;
+                    const uint32_t xw = x[k];
+                    const float4* r4 = reinterpret_cast<const float4*>(srow + 32 * k);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const float4 v = r4[t];
+                        q0 = fmaf((float)((xw >> (4 * t)) & 1u), v.x, q0);
+                        q1 = fmaf((float)((xw >> (4 * t + 1)) & 1u), v.y, q1);
+                        q2s = fmaf((float)((xw >> (4 * t + 2)) & 1u), v.z, q2s);
+                        q3 = fmaf((float)((xw >> (4 * t + 3)) & 1u), v.w, q3);
                     }
                 }
+                const float q = __fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2s, q3));
                 // the warp leaves together: tcgen05.ld below needs all 32 lanes
                 const bool ok = __all_sync(0xffffffffu, mbar_wait(&afull[buf], ((uint32_t)acc_epi >> 1) & 1u, abort_flag));
                 if (!ok) {
@@ -368,25 +376,28 @@ energy_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams p)
                     break;
                 }
                 tc_fence_after();
-                float cacc = 0.f, ccomp = 0.f;
+                float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
                 const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256);
+                uint32_t xr[8];
 #pragma unroll
-                for (int ch = 0; ch < 8; ++ch) {
-                    if (ch >= nch) break;
+                for (int k = 0; k < 8; ++k) xr[k] = x[k];
+#pragma unroll 1
+                for (int ch = 0; ch < nch; ++ch) {
                     uint32_t v[32];
                     tmem_ld32(tbase + (uint32_t)(ch * 32), v);
                     tmem_ld_wait();
-                    const uint32_t xw = x[ch];
+                    const uint32_t xw = xr[0];
 #pragma unroll
-                    for (int t = 0; t < 32; ++t) {
-                        if ((xw >> t) & 1u) {
-                            const float y = __fsub_rn(__uint_as_float(v[t]), ccomp);
-                            const float s = __fadd_rn(cacc, y);
-                            ccomp = __fsub_rn(__fsub_rn(s, cacc), y);
-                            cacc = s;
-                        }
+                    for (int k = 0; k < 7; ++k) xr[k] = xr[k + 1];
+#pragma unroll
+                    for (int t = 0; t < 32; t += 4) {
+                        c0 = fmaf((float)((xw >> t) & 1u), __uint_as_float(v[t]), c0);
+                        c1 = fmaf((float)((xw >> (t + 1)) & 1u), __uint_as_float(v[t + 1]), c1);
+                        c2 = fmaf((float)((xw >> (t + 2)) & 1u), __uint_as_float(v[t + 2]), c2);
+                        c3 = fmaf((float)((xw >> (t + 3)) & 1u), __uint_as_float(v[t + 3]), c3);
                     }
                 }
+                const float cacc = __fadd_rn(__fadd_rn(c0, c1), __fadd_rn(c2, c3));
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&aempty[buf]);
@@ -444,7 +455,8 @@ __global__ void energy_tc_finalize(const float* __restrict__ Epart, int B, int T
 
 static size_t tc_smem_bytes(int NJ, int KP)
 {
-    return 1024 + (size_t)(KP / kTcKB) * 16384 + (size_t)kTcStages * NJ * 128 + 256 + 4 * 4 * (size_t)NJ;
+    return 1024 + (size_t)(KP / kTcKB) * 16384 + (size_t)kTcStages * NJ * 128 + 256 +
+           4 * 4 * (size_t)((NJ + 31) & ~31);
 }
 
 bool tc_supported(const hobo_instance* h)

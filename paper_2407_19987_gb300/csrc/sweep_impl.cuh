@@ -1,5 +1,6 @@
 // Metropolis sweep kernels (included by the sweep translation units).
 #pragma once
+#include <algorithm>
 #include "hobo_internal.h"
 #include "hobo_dev.cuh"
 
@@ -28,6 +29,7 @@ struct SweepDev {
     uint32_t* bestX;
     float* bestE;
     int64_t* accepts;
+    int64_t* coef_bytes;
     const int32_t* bptr;
     const int32_t* rtgt;
     const int32_t* rbeg;
@@ -72,8 +74,8 @@ constexpr int kSweepWarps = 8;
 // 128-wide chunk (NC chunks); rows are visited in ascending order, 8 at a
 // time with their loads in flight together.
 template <int WMAX, int NC>
-__device__ __forceinline__ void dense_update(const SweepDev& p, float* __restrict__ g,
-                                             const uint32_t (&x)[WMAX], int i, float delta, int lane)
+__device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __restrict__ g,
+                                                const uint32_t (&x)[WMAX], int i, float delta, int lane)
 {
     const int N = p.N, P = p.P, W = p.W;
     const float* __restrict__ slab = p.S3 + (int64_t)i * N * P;
@@ -81,6 +83,7 @@ __device__ __forceinline__ void dense_update(const SweepDev& p, float* __restric
 #pragma unroll
     for (int k = 0; k < WMAX; ++k) pop += __popc(x[k]);
     const bool comp = 2 * pop > N;
+    const int64_t bytes = (int64_t)(comp ? N - pop : pop) * P * 4 + (comp ? 2 : 1) * (int64_t)P * 4;
     float4 acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -137,16 +140,18 @@ __device__ __forceinline__ void dense_update(const SweepDev& p, float* __restric
         for (int q = 0; q < 4; ++q)
             if (j + q < N) g[j + q] = __fadd_rn(g[j + q], __fmul_rn(delta, __fadd_rn(s4[q], a4[q])));
     }
+    return bytes;
 }
 
 // Sparse update for a flip of bit i: lanes take target records; each sums
 // the coefficients of its entries whose conditions are all set.
 template <int KU>
-__device__ __forceinline__ void sparse_update(const SweepDev& p, float* __restrict__ g,
-                                              const uint32_t* __restrict__ bs, int i, float delta,
-                                              int lane)
+__device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __restrict__ g,
+                                                 const uint32_t* __restrict__ bs, int i, float delta,
+                                                 int lane)
 {
     const int r0 = p.bptr[i], r1 = p.bptr[i + 1];
+    const int64_t bytes = (int64_t)(r1 - r0) * 12 + (int64_t)(p.rbeg[r1] - p.rbeg[r0]) * (4 + 2 * KU);
     for (int r = r0 + lane; r < r1; r += 32) {
         const int j = p.rtgt[r];
         const int e0 = p.rbeg[r], e1 = p.rbeg[r + 1];
@@ -163,6 +168,7 @@ __device__ __forceinline__ void sparse_update(const SweepDev& p, float* __restri
         }
         g[j] = __fadd_rn(g[j], __fmul_rn(delta, acc));
     }
+    return bytes;
 }
 
 template <int WMAX, bool DENSE, int KU>
@@ -179,7 +185,8 @@ sweep_tuned_kernel(const SweepDev p)
     uint32_t* bs = reinterpret_cast<uint32_t*>(g + NPAD);   // bits + sentinel (sparse lookups)
 
     for (int j = lane; j < N; j += 32) g[j] = p.g[(int64_t)b * N + j];
-    uint32_t x[WMAX], bx[WMAX];
+    uint32_t x[WMAX];
+    uint32_t* bxs = bs + (WMAX + 1);                    // best bits of this state
 #pragma unroll
     for (int k = 0; k < WMAX; ++k) {
         uint32_t v = (k < W) ? p.X[(int64_t)b * W + k] : 0u;
@@ -188,13 +195,8 @@ sweep_tuned_kernel(const SweepDev p)
         x[k] = v;
     }
     float E = p.E[b], Eb = E;
-#pragma unroll
-    for (int k = 0; k < WMAX; ++k) bx[k] = x[k];
-    if (p.resume) {
-#pragma unroll
-        for (int k = 0; k < WMAX; ++k) bx[k] = (k < W) ? p.bestX[(int64_t)b * W + k] : 0u;
-        Eb = p.bestE[b];
-    }
+    for (int k = lane; k < W; k += 32) bxs[k] = p.resume ? p.bestX[(int64_t)b * W + k] : sel_word(x, k);
+    if (p.resume) Eb = p.bestE[b];
     const int wsent = N >> 5;
     const uint32_t sent = 1u << (N & 31);
     if (!DENSE) {
@@ -207,16 +209,28 @@ sweep_tuned_kernel(const SweepDev p)
     __syncwarp();
 
     long long nacc = 0;
+    int64_t nbytes = 0;
     for (int s = 0; s < p.sweeps; ++s) {
         const float beta = __ldg(p.beta + s);
         const uint32_t sw = (uint32_t)(p.sweep0 + s);
+        u32x4 r4 = {0u, 0u, 0u, 0u};
         for (int w = 0; w < W; ++w) {
             uint32_t cw = sel_word(x, w);
             const int nbits = min(32, N - 32 * w);
-            // the draw of bit 32w + lane: word (lane % 4) of counter (8w + lane/4, s, b, 0)
-            const u32x4 r = philox10((uint32_t)(8 * w + (lane >> 2)), sw, (uint32_t)b,
-                                     kStreamMetropolis, p.k0, p.k1);
-            const uint32_t rw = pick4(r, lane & 3);
+            // The draw of bit i = 32w + t is word (i % 4) of the Philox block
+            // with counter (i / 4, s, b, 0).  Every fourth word, lane L
+            // computes block 8 * (w + L / 8) + L % 8, covering words w..w+3;
+            // lane t of word w' then takes its block from lane
+            // 8 * (w' - w0) + t / 4.
+            if ((w & 3) == 0)
+                r4 = philox10((uint32_t)(8 * w + lane), sw, (uint32_t)b, kStreamMetropolis, p.k0, p.k1);
+            const int src = 8 * (w & 3) + (lane >> 2);
+            const uint32_t ra = __shfl_sync(0xffffffffu, r4.a, src);
+            const uint32_t rb = __shfl_sync(0xffffffffu, r4.b, src);
+            const uint32_t rc = __shfl_sync(0xffffffffu, r4.c, src);
+            const uint32_t rd = __shfl_sync(0xffffffffu, r4.d, src);
+            const int e = lane & 3;
+            const uint32_t rw = e == 0 ? ra : (e == 1 ? rb : (e == 2 ? rc : rd));
             int t0 = 0;
             while (true) {
                 const int i = 32 * w + lane;
@@ -238,16 +252,15 @@ sweep_tuned_kernel(const SweepDev p)
                 set_word(x, w, cw);
                 if (E < Eb) {
                     Eb = E;
-#pragma unroll
-                    for (int k = 0; k < WMAX; ++k) bx[k] = x[k];
+                    for (int k = lane; k < W; k += 32) bxs[k] = sel_word(x, k);
                 }
                 const int fi = 32 * w + f;
                 if (DENSE) {
-                    dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1)>(p, g, x, fi, delta, lane);
+                    nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1)>(p, g, x, fi, delta, lane);
                 } else {
                     if (lane == 0) bs[w] = cw | (w == wsent ? sent : 0u);
                     __syncwarp();
-                    sparse_update<KU>(p, g, bs, fi, delta, lane);
+                    nbytes += sparse_update<KU>(p, g, bs, fi, delta, lane);
                 }
                 __syncwarp();
                 t0 = f + 1;
@@ -259,7 +272,7 @@ sweep_tuned_kernel(const SweepDev p)
 
     for (int k = lane; k < W; k += 32) {
         p.X[(int64_t)b * W + k] = sel_word(x, k);
-        p.bestX[(int64_t)b * W + k] = sel_word(bx, k);
+        p.bestX[(int64_t)b * W + k] = bxs[k];
     }
     if (p.write_g)
         for (int j = lane; j < N; j += 32) p.g[(int64_t)b * N + j] = g[j];
@@ -267,6 +280,7 @@ sweep_tuned_kernel(const SweepDev p)
         p.E[b] = E;
         p.bestE[b] = Eb;
         if (p.accepts) p.accepts[b] += nacc;
+        if (p.coef_bytes) p.coef_bytes[b] += nbytes;
     }
 }
 
@@ -279,6 +293,7 @@ inline cudaError_t run_tuned(const SweepDev& p, cudaStream_t st)
     auto kern = sweep_tuned_kernel<WMAX, DENSE, KU>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+
     const unsigned grid = (unsigned)((p.B + kSweepWarps - 1) / kSweepWarps);
     kern<<<grid, kSweepWarps * 32, sm, st>>>(p);
     return cudaGetLastError();

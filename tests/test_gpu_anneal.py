@@ -85,9 +85,9 @@ def test_anneal_tuned_equals_plain(name, maker, flags, B, sched):
     inst = maker()
     betas = W.geometric_betas(*sched)
     h = gpuh.make(inst, flags)
-    a = _run(h, 99, B, betas, TUNED)
-    b = _run(h, 99, B, betas, PLAIN)
-    for k in ("bestX", "X", "accepts", "bestE"):
+    a = _run(h, 99, B, betas, TUNED, want_bytes=True)
+    b = _run(h, 99, B, betas, PLAIN, want_bytes=True)
+    for k in ("bestX", "X", "accepts", "bestE", "coef_bytes"):
         np.testing.assert_array_equal(a[k].cpu().numpy(), b[k].cpu().numpy())
     np.testing.assert_array_equal(a["E"].cpu().numpy(), b["E"].cpu().numpy())
     # the reported best energies are the float64 energies of the best states
