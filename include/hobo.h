@@ -143,6 +143,26 @@ int hobo_energy_path(hobo_h h, const uint32_t* X, int B, float* E, float* dE, in
  */
 int hobo_energy_fp64(hobo_h h, const uint32_t* X, int B, double* E, void* stream);
 
+/*
+ * hobo_energy_fp64_noalloc -- hobo_energy_fp64 that allocates nothing.
+ * (The paper has no counterpart: this serves callers that cannot let the
+ * library allocate device memory, e.g. applications whose GPU memory is
+ * fully reserved by their own pool, or loops that must not risk an
+ * allocation's synchronisation or pool growth.)
+ *   Same arguments and results as hobo_energy_fp64, for B <= HOBO_NOALLOC_MAX_B
+ *   states; larger B returns HOBO_ERR_ARG and does nothing.
+ *   Scratch: a fixed 512 KiB array in device memory that every GPU loading
+ *   the library holds until the process exits.  The first call on a device
+ *   looks up that array's device address (make that first call before any
+ *   stream capture).  Each call clears the part it uses, on `stream`.  All
+ *   calls share the array: calls whose GPU work overlaps (other streams,
+ *   no ordering) race and give wrong results, so order them.
+ *   The instance must live on the current device (else HOBO_ERR_ARG).
+ *   Errors: HOBO_ERR_ARG, HOBO_ERR_CUDA.
+ */
+#define HOBO_NOALLOC_MAX_B 65536
+int hobo_energy_fp64_noalloc(hobo_h h, const uint32_t* X, int B, double* E, void* stream);
+
 /* ---- annealing -------------------------------------------------------- */
 
 #define HOBO_ANNEAL_TUNED  0  /* persistent kernel, states in shared memory */

@@ -36,6 +36,7 @@ HOBO_ANNEAL_PLAIN = 1
 PATH_AUTO, PATH_TERMS, PATH_TENSOR_CORE = 0, 1, 2
 
 HOBO_MAX_ORDER = 8
+HOBO_NOALLOC_MAX_B = 65536
 
 
 class HoboError(RuntimeError):
@@ -79,6 +80,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     L.hobo_energy_fp64.argtypes = [P, P, I, P, P]
     L.hobo_anneal.argtypes = [P, U64, I, P, I, P, P, C.POINTER(hobo_anneal_opts), P]
     L.hobo_check.argtypes = [P, P]
+    L.hobo_energy_fp64_noalloc.argtypes = [P, P, I, P, P]
+    L.hobo_energy_fp64_noalloc.restype = I
     L.hobo_last_error.restype = C.c_char_p
     L.hobo_version.restype = C.c_char_p
     for name in ("hobo_create", "hobo_create_terms", "hobo_info", "hobo_energy", "hobo_energy_path",
@@ -176,6 +179,17 @@ class Instance:
         """Synchronize the stream and raise HoboError(HOBO_ERR_TIMEOUT) if a
         kernel of this instance gave up a bounded wait."""
         _check(load_library().hobo_check(self._h, _stream(stream)))
+
+    def energy_fp64_noalloc(self, X, E=None, stream=None):
+        """hobo_energy_fp64_noalloc: float64 re-score using the library's fixed
+        device scratch (no allocation in the library; at most
+        HOBO_NOALLOC_MAX_B states).  E: optional preallocated f64 output."""
+        import torch
+        B = X.shape[0]
+        if E is None:
+            E = torch.empty(B, dtype=torch.float64, device=X.device)
+        _check(load_library().hobo_energy_fp64_noalloc(self._h, _ptr(X), B, _ptr(E), _stream(stream)))
+        return E
 
     def energy_fp64(self, X, stream=None):
         import torch

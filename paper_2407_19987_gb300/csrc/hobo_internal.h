@@ -78,6 +78,9 @@ cudaError_t launch_energy_terms(const hobo_instance* h, const uint32_t* X, int B
 
 cudaError_t launch_energy_fp64(const hobo_instance* h, const uint32_t* X, int B, double* E,
                                cudaStream_t st);
+// acc: device, B zeroed 64-bit accumulators owned by the caller
+cudaError_t launch_energy_fp64_into(const hobo_instance* h, const uint32_t* X, int B, double* E,
+                                    unsigned long long* acc, cudaStream_t st);
 
 struct SweepArgs {
     int B = 0, sweeps = 0, sweep0 = 0, resume = 0, S = 32;

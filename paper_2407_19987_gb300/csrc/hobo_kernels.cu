@@ -275,6 +275,36 @@ cudaError_t launch_energy_fp64(const hobo_instance* h, const uint32_t* X, int B,
     return e;
 }
 
+// The same re-score with caller-owned accumulators: acc must hold B zeroed
+// 64-bit words on the device; nothing is allocated here.
+cudaError_t launch_energy_fp64_into(const hobo_instance* h, const uint32_t* X, int B, double* E,
+                                    unsigned long long* acc, cudaStream_t st)
+{
+    if (B == 0) return cudaSuccess;
+    const int64_t M = h->d.M;
+    const int tiles = (B + 31) / 32;
+    int slices = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * h->num_sms + tiles - 1) / tiles,
+                                                             (M + 4095) / 4096));
+    const int64_t per = (M + slices - 1) / std::max(slices, 1);
+    cudaError_t e = cudaSuccess;
+    if (M > 0) {
+        const size_t sm = sizeof(uint32_t) * (((size_t)(h->W + 1) * 32 + 1) & ~(size_t)1) +
+                          sizeof(long long) * (kFixThreads / 32) * 32;
+        if (h->KS == 4)
+            energy_fix_kernel<4><<<dim3(tiles, slices), kFixThreads, sm, st>>>(
+                X, B, h->N, h->W, h->d.tvars, h->d.tfix, M, per, acc);
+        else
+            energy_fix_kernel<8><<<dim3(tiles, slices), kFixThreads, sm, st>>>(
+                X, B, h->N, h->W, h->d.tvars, h->d.tfix, M, per, acc);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        energy_fix_finalize<<<(B + 255) / 256, 256, 0, st>>>(acc, B, h->d.fix_shift, E);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
 // ---------------------------------------------------------------------------
 // Plain sweep: one thread per state, fields and bits in global memory.
 // ---------------------------------------------------------------------------
