@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--mode", default="tuned", choices=["tuned", "plain"])
     ap.add_argument("--cpu-states", type=int, default=8, help="oracle sample size (states)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", default=None, choices=["sweep", "tc", "fix"],
+                    help="run one small case of one kernel (for profilers) and exit")
+    ap.add_argument("--case-states", type=int, default=4096)
+    ap.add_argument("--case-sweeps", type=int, default=30)
     return ap.parse_args()
 
 
@@ -294,8 +298,35 @@ def run_ours(a):
     return 0
 
 
+def run_kernel_case(a):
+    """One small case of one kernel of the dense workload, for profilers:
+    sweep: an anneal of --case-states states over the first --case-sweeps
+    sweeps; tc: two tensor-core contractions of 4096 random states; fix: two
+    exact re-scores of 4096 random states."""
+    import torch
+
+    import paper_2407_19987_gb300 as H
+    inst, betas, B, S = workload()
+    h = H.Instance.from_terms(inst.idx, inst.coef, inst.N)
+    if a.kernel_case == "sweep":
+        h.anneal(2, a.case_states, betas[:a.case_sweeps])
+    else:
+        X = torch.from_numpy(W.pack_bits(W.random_states(1, 4096, inst.N)).view(np.int32)).cuda()
+        for _ in range(2):
+            if a.kernel_case == "tc":
+                h.energy(X, path=H.PATH_TENSOR_CORE)
+            else:
+                h.energy_fp64(X)
+    torch.cuda.synchronize()
+    h.check()
+    print("kernel case done:", a.kernel_case)
+    return 0
+
+
 def main():
     a = parse()
+    if a.kernel_case:
+        return run_kernel_case(a)
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

@@ -93,7 +93,8 @@ static int upload(T** dst, const std::vector<T>& src)
 static void free_layouts(DevLayouts& d)
 {
     void* ptrs[] = {d.tvars, d.tcoef32, d.tcoef64, d.tfix, d.fptr, d.fvars, d.fcoef, d.bptr, d.rtgt,
-                    d.rbeg, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf};
+                    d.rbeg, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf,
+                    d.C3fix, d.S2fix, d.afix, d.pair_m, d.pair_j};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DevLayouts{};
@@ -232,6 +233,24 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
                 for (auto& pm : perm)
                     S3[((size_t)v[pm[0]] * N + v[pm[1]]) * P + v[pm[2]]] = c;
             }
+        }
+        {
+            // exact fixed-point copies for the structured re-score
+            std::vector<long long> c3((size_t)N * N * N, 0), c2((size_t)N * N, 0), c1((size_t)N, 0);
+            for (auto& e : mono) {
+                const long long f = std::llrint(std::ldexp(e.c, d.fix_shift));
+                if (e.m.d == 1) c1[e.m.v[0]] = f;
+                else if (e.m.d == 2) c2[(size_t)e.m.v[0] * N + e.m.v[1]] = f;
+                else c3[((size_t)e.m.v[0] * N + e.m.v[1]) * N + e.m.v[2]] = f;
+            }
+            std::vector<uint16_t> pm, pj;
+            for (int m = 0; m < N; ++m)
+                for (int j = m + 1; j < N; ++j) { pm.push_back((uint16_t)m); pj.push_back((uint16_t)j); }
+            if (pm.empty()) { pm.push_back(0); pj.push_back(0); }
+            int rc2;
+            if ((rc2 = upload(&d.C3fix, c3)) || (rc2 = upload(&d.S2fix, c2)) || (rc2 = upload(&d.afix, c1)) ||
+                (rc2 = upload(&d.pair_m, pm)) || (rc2 = upload(&d.pair_j, pj)))
+                return rc2;
         }
         std::vector<double> colsum((size_t)N * P, 0.0);
         for (auto& e : mono)

@@ -45,6 +45,14 @@ struct DevLayouts {
     float* S2 = nullptr;
     float* S3 = nullptr;
     float* S3col = nullptr;      // [N][P]: S3col[i][j] = sum_l S3[i][l][j]
+    // exact re-score of dense instances: fixed-point coefficients (scale
+    // 2^fix_shift) C3fix[m][j][l] for m < j < l (else 0), S2fix[m][j] for
+    // m < j, afix[m]; and the list of pairs m < j
+    long long* C3fix = nullptr;
+    long long* S2fix = nullptr;
+    long long* afix = nullptr;
+    uint16_t* pair_m = nullptr;
+    uint16_t* pair_j = nullptr;
     // bf16 planes [nsplit][N][NJ][KP]: plane q, row (m, j), column l;
     // NJ = N rounded up to 16, KP = N rounded up to 64, zero padded.
     uint16_t* S3bf = nullptr;

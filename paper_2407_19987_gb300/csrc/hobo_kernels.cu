@@ -236,6 +236,79 @@ energy_fix_kernel(const uint32_t* __restrict__ X, int B, int N, int W,
     }
 }
 
+// Dense order-3 instances: the same exact fixed-point sums, structured by
+// the dense layout.  Lanes are 32 states; warps take pairs (m, j), m < j.
+// For a pair the quadratic coefficient is added where both bits are set, and
+// the cubic row C[m][j][l], l > j, is loaded once per 32 columns and
+// broadcast lane by lane, so every coefficient is read once per 32 states.
+template <int WMAX>
+__global__ void __launch_bounds__(kFixThreads)
+energy_fix_dense_kernel(const uint32_t* __restrict__ X, int B, int N, int W,
+                        const long long* __restrict__ C3, const long long* __restrict__ S2f,
+                        const long long* __restrict__ af, const uint16_t* __restrict__ pm,
+                        const uint16_t* __restrict__ pj, int npairs, int per_slice,
+                        unsigned long long* __restrict__ acc)
+{
+    __shared__ long long red[kFixThreads];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int b = blockIdx.x * 32 + lane;
+    uint32_t x[WMAX];
+#pragma unroll
+    for (int k = 0; k < WMAX; ++k) {
+        uint32_t v = (b < B && k < W) ? X[(int64_t)b * W + k] : 0u;
+        const int rem = N - 32 * k;
+        if (rem <= 0) v = 0u; else if (rem < 32) v &= (1u << rem) - 1u;
+        x[k] = v;
+    }
+    long long s = 0;
+    if (blockIdx.y == 0 && warp == 0)
+        for (int m = 0; m < N; ++m)
+            if ((sel_word(x, m >> 5) >> (m & 31)) & 1u) s += __ldg(af + m);
+    const int p0 = blockIdx.y * per_slice, p1 = min(npairs, p0 + per_slice);
+    for (int q = p0 + warp; q < p1; q += nwarps) {
+        const int m = pm[q], j = pj[q];
+        const bool mj = ((sel_word(x, m >> 5) >> (m & 31)) & (sel_word(x, j >> 5) >> (j & 31)) & 1u) != 0u;
+        if (!__any_sync(0xffffffffu, mj)) continue;
+        if (mj) s += __ldg(S2f + (int64_t)m * N + j);
+        const long long* row = C3 + ((int64_t)m * N + j) * N;
+        for (int k = (j + 1) >> 5; k < W; ++k) {
+            const int l = 32 * k + lane;
+            const long long c = l < N ? __ldg(row + l) : 0ll;
+            const uint32_t xw = mj ? sel_word(x, k) : 0u;   // no cubic term without x_m x_j
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const long long ct = __shfl_sync(0xffffffffu, c, t);
+                if ((xw >> t) & 1u) s += ct;
+            }
+        }
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (warp == 0 && b < B) {
+        long long tot = 0;
+        for (int q = 0; q < nwarps; ++q) tot += red[q * 32 + lane];
+        atomicAdd(acc + b, (unsigned long long)tot);
+    }
+}
+
+static cudaError_t launch_fix_dense(const hobo_instance* h, const uint32_t* X, int B,
+                                    unsigned long long* acc, cudaStream_t st)
+{
+    const auto& d = h->d;
+    const int tiles = (B + 31) / 32;
+    const int npairs = h->N * (h->N - 1) / 2;
+    const int slices = std::max(1, std::min((4 * h->num_sms + tiles - 1) / tiles, (npairs + 63) / 64));
+    const int per = (npairs + slices - 1) / slices;
+    const dim3 grid(tiles, slices);
+    if (h->W <= 8)
+        energy_fix_dense_kernel<8><<<grid, kFixThreads, 0, st>>>(X, B, h->N, h->W, d.C3fix, d.S2fix, d.afix,
+                                                                 d.pair_m, d.pair_j, npairs, per, acc);
+    else
+        energy_fix_dense_kernel<16><<<grid, kFixThreads, 0, st>>>(X, B, h->N, h->W, d.C3fix, d.S2fix, d.afix,
+                                                                  d.pair_m, d.pair_j, npairs, per, acc);
+    return cudaGetLastError();
+}
+
 __global__ void energy_fix_finalize(const unsigned long long* __restrict__ acc, int B, int S,
                                     double* __restrict__ E)
 {
@@ -256,7 +329,9 @@ cudaError_t launch_energy_fp64(const hobo_instance* h, const uint32_t* X, int B,
     cudaError_t e = cudaMallocAsync((void**)&acc, sizeof(unsigned long long) * (size_t)B, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)B, st);
-    if (e == cudaSuccess && M > 0) {
+    if (e == cudaSuccess && h->d.C3fix) {
+        e = launch_fix_dense(h, X, B, acc, st);
+    } else if (e == cudaSuccess && M > 0) {
         const size_t sm = sizeof(uint32_t) * (((size_t)(h->W + 1) * 32 + 1) & ~(size_t)1) +
                           sizeof(long long) * (kFixThreads / 32) * 32;
         if (h->KS == 4)
@@ -287,7 +362,9 @@ cudaError_t launch_energy_fp64_into(const hobo_instance* h, const uint32_t* X, i
                                                              (M + 4095) / 4096));
     const int64_t per = (M + slices - 1) / std::max(slices, 1);
     cudaError_t e = cudaSuccess;
-    if (M > 0) {
+    if (h->d.C3fix) {
+        e = launch_fix_dense(h, X, B, acc, st);
+    } else if (M > 0) {
         const size_t sm = sizeof(uint32_t) * (((size_t)(h->W + 1) * 32 + 1) & ~(size_t)1) +
                           sizeof(long long) * (kFixThreads / 32) * 32;
         if (h->KS == 4)

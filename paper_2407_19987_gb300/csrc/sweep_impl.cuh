@@ -75,7 +75,8 @@ constexpr int kSweepWarps = 8;
 // time with their loads in flight together.
 template <int WMAX, int NC>
 __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __restrict__ g,
-                                                const uint32_t (&x)[WMAX], int i, float delta, int lane)
+                                                const uint32_t (&x)[WMAX], int i, float delta, int lane,
+                                                uint16_t* __restrict__ rows)
 {
     const int N = p.N, P = p.P, W = p.W;
     const float* __restrict__ slab = p.S3 + (int64_t)i * N * P;
@@ -83,43 +84,48 @@ __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __rest
 #pragma unroll
     for (int k = 0; k < WMAX; ++k) pop += __popc(x[k]);
     const bool comp = 2 * pop > N;
-    const int64_t bytes = (int64_t)(comp ? N - pop : pop) * P * 4 + (comp ? 2 : 1) * (int64_t)P * 4;
-    float4 acc[NC];
+    // list of the rows to read, ascending: set bits, or clear bits below N
+    int nrows = 0;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 1
-    for (int k = 0; k < W; ++k) {
-        uint32_t u = sel_word(x, k);
+    for (int k = 0; k < WMAX; ++k) {
+        if (k >= W) break;
+        uint32_t u = x[k];
         if (comp) {
             u = ~u;
             const int rem = N - 32 * k;
             if (rem < 32) u &= (1u << rem) - 1u;
         }
-#pragma unroll 1
-        for (int t0 = 0; t0 < 32; t0 += 8) {
-            const uint32_t ub = (u >> t0) & 0xFFu;
-            if (ub == 0u) continue;
-            float4 v[8][NC];
+        if ((u >> lane) & 1u) rows[nrows + __popc(u & ((1u << lane) - 1u))] = (uint16_t)(32 * k + lane);
+        nrows += __popc(u);
+    }
+    __syncwarp();
+    const int64_t bytes = (int64_t)nrows * P * 4 + (comp ? 2 : 1) * (int64_t)P * 4;
+    float4 acc[NC];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const float* row = slab + (int64_t)(32 * k + t0 + t) * P;
+    for (int c = 0; c < NC; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int r0 = 0; r0 < nrows; r0 += 8) {
+        float4 v[8][NC];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const bool ok = r0 + t < nrows;
+            const float* row = slab + (int64_t)(ok ? rows[r0 + t] : 0) * P;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int j = 128 * c + 4 * lane;
+                v[t][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ok && j < P) v[t][c] = __ldg(reinterpret_cast<const float4*>(row + j));
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (r0 + t < nrows) {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const int j = 128 * c + 4 * lane;
-                    v[t][c] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (((ub >> t) & 1u) && j < P) v[t][c] = __ldg(reinterpret_cast<const float4*>(row + j));
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                if ((ub >> t) & 1u) {
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        acc[c].x = __fadd_rn(acc[c].x, v[t][c].x);
-                        acc[c].y = __fadd_rn(acc[c].y, v[t][c].y);
-                        acc[c].z = __fadd_rn(acc[c].z, v[t][c].z);
-                        acc[c].w = __fadd_rn(acc[c].w, v[t][c].w);
-                    }
+                    acc[c].x = __fadd_rn(acc[c].x, v[t][c].x);
+                    acc[c].y = __fadd_rn(acc[c].y, v[t][c].y);
+                    acc[c].z = __fadd_rn(acc[c].z, v[t][c].z);
+                    acc[c].w = __fadd_rn(acc[c].w, v[t][c].w);
                 }
             }
         }
@@ -181,8 +187,9 @@ sweep_tuned_kernel(const SweepDev p)
     const int b = blockIdx.x * kSweepWarps + warp;       // state of this warp
     if (b >= p.B) return;                                // warp-uniform; no block barriers below
     const int NPAD = (N + 3) & ~3;
-    float* g = sm + (size_t)warp * (NPAD + 4 * (WMAX + 1));
+    float* g = sm + (size_t)warp * (NPAD + 4 * (WMAX + 1) + NPAD / 2);
     uint32_t* bs = reinterpret_cast<uint32_t*>(g + NPAD);   // bits + sentinel (sparse lookups)
+    uint16_t* rows = reinterpret_cast<uint16_t*>(bs + 4 * (WMAX + 1));   // dense: rows to read
 
     for (int j = lane; j < N; j += 32) g[j] = p.g[(int64_t)b * N + j];
     uint32_t x[WMAX];
@@ -256,7 +263,7 @@ sweep_tuned_kernel(const SweepDev p)
                 }
                 const int fi = 32 * w + f;
                 if (DENSE) {
-                    nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1)>(p, g, x, fi, delta, lane);
+                    nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1)>(p, g, x, fi, delta, lane, rows);
                 } else {
                     if (lane == 0) bs[w] = cw | (w == wsent ? sent : 0u);
                     __syncwarp();
@@ -288,7 +295,7 @@ template <int WMAX, bool DENSE, int KU>
 inline cudaError_t run_tuned(const SweepDev& p, cudaStream_t st)
 {
     const int NPAD = (p.N + 3) & ~3;
-    const size_t per_warp = sizeof(float) * (size_t)(NPAD + 4 * (WMAX + 1));
+    const size_t per_warp = sizeof(float) * (size_t)(NPAD + 4 * (WMAX + 1) + NPAD / 2);
     const size_t sm = per_warp * kSweepWarps;
     auto kern = sweep_tuned_kernel<WMAX, DENSE, KU>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
