@@ -72,6 +72,10 @@ __device__ __forceinline__ bool metropolis(float dE, float beta, uint32_t w)
     if (dE <= 0.0f) return true;
     const float a = __fmul_rn(beta, dE);
     const float t = -__fmul_rn(a, __uint_as_float(0x3FB8AA3Bu));   // log2(e)
+    // Shortcut with the same decision: for t < -26, exp2_fixed(t) <
+    // 1.42 * 2^(t + 1/2) < 2^-24, while a nonzero u is at least 2^-24, so
+    // the test can only pass for u == 0, where it passes iff p > 0.
+    if (t < -26.0f && (w >> 8) != 0u) return false;
     const float p = exp2_fixed(t);
     const float u = __fmul_rn((float)(w >> 8), 5.9604644775390625e-8f);  // 2^-24
     return u < p;

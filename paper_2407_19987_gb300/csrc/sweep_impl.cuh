@@ -76,7 +76,7 @@ constexpr int kSweepWarps = 8;
 template <int WMAX, int NC>
 __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __restrict__ g,
                                                 const uint32_t (&x)[WMAX], int i, float delta, int lane,
-                                                uint16_t* __restrict__ rows)
+                                                uint32_t* __restrict__ rows)
 {
     const int N = p.N, P = p.P, W = p.W;
     const float* __restrict__ slab = p.S3 + (int64_t)i * N * P;
@@ -84,7 +84,8 @@ __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __rest
 #pragma unroll
     for (int k = 0; k < WMAX; ++k) pop += __popc(x[k]);
     const bool comp = 2 * pop > N;
-    // list of the rows to read, ascending: set bits, or clear bits below N
+    // offsets (in floats, within the slab) of the rows to read, ascending:
+    // set bits, or clear bits below N
     int nrows = 0;
 #pragma unroll
     for (int k = 0; k < WMAX; ++k) {
@@ -95,47 +96,61 @@ __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __rest
             const int rem = N - 32 * k;
             if (rem < 32) u &= (1u << rem) - 1u;
         }
-        if ((u >> lane) & 1u) rows[nrows + __popc(u & ((1u << lane) - 1u))] = (uint16_t)(32 * k + lane);
+        if ((u >> lane) & 1u) rows[nrows + __popc(u & ((1u << lane) - 1u))] = (uint32_t)((32 * k + lane) * P);
         nrows += __popc(u);
     }
     __syncwarp();
     const int64_t bytes = (int64_t)nrows * P * 4 + (comp ? 2 : 1) * (int64_t)P * 4;
-    float4 acc[NC];
+    // this lane's columns: 4 consecutive targets in each 128-wide chunk
+    const float* base[NC];
+    bool jv[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < NC; ++c) {
+        jv[c] = 128 * c + 4 * lane < P;
+        base[c] = slab + (jv[c] ? 128 * c + 4 * lane : 0);
+    }
+    // accumulators as packed float pairs: add.rn.f32x2 rounds each half
+    // exactly like a scalar round-to-nearest add
+    uint64_t acc[NC][2];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { acc[c][0] = 0ull; acc[c][1] = 0ull; }
+    int r0 = 0;
 #pragma unroll 1
-    for (int r0 = 0; r0 < nrows; r0 += 8) {
-        float4 v[8][NC];
+    for (; r0 + 8 <= nrows; r0 += 8) {
+        const uint4 o0 = *reinterpret_cast<const uint4*>(rows + r0);
+        const uint4 o1 = *reinterpret_cast<const uint4*>(rows + r0 + 4);
+        const uint32_t off[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+        ulonglong2 v[8][NC];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const bool ok = r0 + t < nrows;
-            const float* row = slab + (int64_t)(ok ? rows[r0 + t] : 0) * P;
+        for (int t = 0; t < 8; ++t)
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                v[t][c] = jv[c] ? __ldg(reinterpret_cast<const ulonglong2*>(base[c] + off[t])) : make_ulonglong2(0ull, 0ull);
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const int j = 128 * c + 4 * lane;
-                v[t][c] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (ok && j < P) v[t][c] = __ldg(reinterpret_cast<const float4*>(row + j));
+                asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc[c][0]) : "l"(v[t][c].x));
+                asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc[c][1]) : "l"(v[t][c].y));
             }
-        }
+    }
+#pragma unroll 1
+    for (; r0 < nrows; ++r0) {
+        const uint32_t off = rows[r0];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            if (r0 + t < nrows) {
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    acc[c].x = __fadd_rn(acc[c].x, v[t][c].x);
-                    acc[c].y = __fadd_rn(acc[c].y, v[t][c].y);
-                    acc[c].z = __fadd_rn(acc[c].z, v[t][c].z);
-                    acc[c].w = __fadd_rn(acc[c].w, v[t][c].w);
-                }
-            }
+        for (int c = 0; c < NC; ++c) {
+            const ulonglong2 v = jv[c] ? __ldg(reinterpret_cast<const ulonglong2*>(base[c] + off)) : make_ulonglong2(0ull, 0ull);
+            asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc[c][0]) : "l"(v.x));
+            asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc[c][1]) : "l"(v.y));
         }
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const int j = 128 * c + 4 * lane;
-        if (j >= P) continue;
+        if (!jv[c]) continue;
         const float4 s2 = __ldg(reinterpret_cast<const float4*>(p.S2 + (int64_t)i * P + j));
-        float4 d = acc[c];
+        float4 d = make_float4(__uint_as_float((uint32_t)acc[c][0]), __uint_as_float((uint32_t)(acc[c][0] >> 32)),
+                               __uint_as_float((uint32_t)acc[c][1]), __uint_as_float((uint32_t)(acc[c][1] >> 32)));
         if (comp) {
             const float4 cs = __ldg(reinterpret_cast<const float4*>(p.S3col + (int64_t)i * P + j));
             d = make_float4(__fsub_rn(cs.x, d.x), __fsub_rn(cs.y, d.y), __fsub_rn(cs.z, d.z), __fsub_rn(cs.w, d.w));
@@ -187,9 +202,11 @@ sweep_tuned_kernel(const SweepDev p)
     const int b = blockIdx.x * kSweepWarps + warp;       // state of this warp
     if (b >= p.B) return;                                // warp-uniform; no block barriers below
     const int NPAD = (N + 3) & ~3;
-    float* g = sm + (size_t)warp * (NPAD + 4 * (WMAX + 1) + NPAD / 2);
+    // per-warp region, every part a multiple of 16 bytes: fields, bits and
+    // best bits, then the dense update's list of row offsets (read 8 at a time)
+    float* g = sm + (size_t)warp * (2 * NPAD + 4 * (WMAX + 1) + 8);
     uint32_t* bs = reinterpret_cast<uint32_t*>(g + NPAD);   // bits + sentinel (sparse lookups)
-    uint16_t* rows = reinterpret_cast<uint16_t*>(bs + 4 * (WMAX + 1));   // dense: rows to read
+    uint32_t* rows = bs + 4 * (WMAX + 1);                   // dense: offsets of the rows to read
 
     for (int j = lane; j < N; j += 32) g[j] = p.g[(int64_t)b * N + j];
     uint32_t x[WMAX];
@@ -295,7 +312,7 @@ template <int WMAX, bool DENSE, int KU>
 inline cudaError_t run_tuned(const SweepDev& p, cudaStream_t st)
 {
     const int NPAD = (p.N + 3) & ~3;
-    const size_t per_warp = sizeof(float) * (size_t)(NPAD + 4 * (WMAX + 1) + NPAD / 2);
+    const size_t per_warp = sizeof(float) * (size_t)(2 * NPAD + 4 * (WMAX + 1) + 8);
     const size_t sm = per_warp * kSweepWarps;
     auto kern = sweep_tuned_kernel<WMAX, DENSE, KU>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
