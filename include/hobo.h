@@ -228,6 +228,62 @@ int hobo_anneal(hobo_h h, uint64_t seed, int B, const float* beta, int sweeps,
  */
 int hobo_check(hobo_h h, void* stream);
 
+/* ---- batches of instances ---------------------------------------------- */
+
+/*
+ * A batch plan anneals many instances of uneven size together (the tensor
+ * batch system of Sec. IV.C applied across instances).  It owns, per
+ * instance t, B[t] states laid out in contiguous blocks: state block t
+ * starts at state offset soff[t] = B[0] + ... + B[t-1] (energies) and at
+ * word offset xoff[t] = sum_{u<t} B[u] * W_u (packed states, W_u =
+ * ceil(N_u/32)); hobo_batch_layout returns both.  The instances must stay
+ * alive while the plan exists.
+ *
+ * hobo_batch_anneal, mode HOBO_BATCH_GRAPH: the sweep of all instances runs
+ * as one persistent kernel per layout kind (dense / sparse of order <= 3 /
+ * order 4 / order 5..8) whose warps take (instance, state) items from a
+ * queue sorted by decreasing cost; initial states, contraction, sweep and
+ * re-score are captured once into a CUDA graph (rebuilt only when the
+ * launch shape or the schedule buffer changes) and replayed on `stream`.
+ * On the first call the launch shape (warps per CTA, CTAs per SM) is picked
+ * by timing a few sweeps of each candidate (synchronous).  Modes
+ * HOBO_BATCH_PER_INSTANCE_TUNED / _PLAIN run one launch sequence per
+ * instance with the tuned / plain sweep instead.  In every mode state b of
+ * instance t is annealed exactly as hobo_anneal(hs[t], seeds[t], ...) would
+ * anneal state b.
+ *   seeds  host [n];  beta host [sweeps]
+ *   bestX  device, xoff[n-1] + B[n-1]*W_{n-1} words;  bestE device double
+ *          [total states], float64 re-scored
+ * Calls synchronise `stream` briefly to upload the instance descriptors.
+ * Errors: HOBO_ERR_ARG, HOBO_ERR_OOM, HOBO_ERR_CUDA.
+ */
+typedef struct hobo_batch* hobo_batch_h;
+
+#define HOBO_BATCH_GRAPH               0
+#define HOBO_BATCH_PER_INSTANCE_TUNED  1
+#define HOBO_BATCH_PER_INSTANCE_PLAIN  2
+
+typedef struct {
+    int mode;             /* HOBO_BATCH_* */
+    int no_autotune;      /* 1: keep the current launch shape */
+    int warps_per_cta;    /* > 0: force warps per CTA (1..8) */
+    int ctas_per_sm;      /* > 0: force CTAs per SM */
+    int64_t* accepts;     /* device [total] or NULL: accepted flips (added to) */
+    uint32_t* X_out;      /* device, same layout as bestX, or NULL: final states */
+    float* E_out;         /* device [total] or NULL: final float32 energies */
+    void* ev_begin;       /* cudaEvent_t or NULL: recorded before the work */
+    void* ev_end;         /* cudaEvent_t or NULL: recorded after the work */
+} hobo_batch_opts;
+
+int hobo_batch_create(hobo_batch_h* out, const hobo_h* hs, int n, const int* B);
+void hobo_batch_destroy(hobo_batch_h bh);
+int hobo_batch_layout(hobo_batch_h bh, int64_t* state_offset, int64_t* word_offset);
+int hobo_batch_anneal(hobo_batch_h bh, const uint64_t* seeds, const float* beta, int sweeps,
+                      uint32_t* bestX, double* bestE, const hobo_batch_opts* opts, void* stream);
+/* Launch shape chosen for layout group `group` (0-based, in the order dense,
+ * sparse order <= 3, order 4, order 5..8, skipping empty groups). */
+int hobo_batch_launch_shape(hobo_batch_h bh, int group, int* warps_per_cta, int* ctas);
+
 /* Human-readable message of the last error on this thread ("" if none). */
 const char* hobo_last_error(void);
 

@@ -51,6 +51,17 @@ class hobo_info_t(C.Structure):
                 ("abs_sum", C.c_double)]
 
 
+HOBO_BATCH_GRAPH = 0
+HOBO_BATCH_PER_INSTANCE_TUNED = 1
+HOBO_BATCH_PER_INSTANCE_PLAIN = 2
+
+
+class hobo_batch_opts(C.Structure):
+    _fields_ = [("mode", C.c_int), ("no_autotune", C.c_int), ("warps_per_cta", C.c_int),
+                ("ctas_per_sm", C.c_int), ("accepts", C.c_void_p), ("X_out", C.c_void_p),
+                ("E_out", C.c_void_p), ("ev_begin", C.c_void_p), ("ev_end", C.c_void_p)]
+
+
 class hobo_anneal_opts(C.Structure):
     _fields_ = [("mode", C.c_int), ("states_per_block", C.c_int), ("sweep0", C.c_int),
                 ("resume", C.c_int), ("X_io", C.c_void_p), ("bestE32_io", C.c_void_p),
@@ -82,6 +93,14 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     L.hobo_check.argtypes = [P, P]
     L.hobo_energy_fp64_noalloc.argtypes = [P, P, I, P, P]
     L.hobo_energy_fp64_noalloc.restype = I
+    L.hobo_batch_create.argtypes = [C.POINTER(P), P, I, P]
+    L.hobo_batch_destroy.argtypes = [P]
+    L.hobo_batch_destroy.restype = None
+    L.hobo_batch_layout.argtypes = [P, P, P]
+    L.hobo_batch_anneal.argtypes = [P, P, P, I, P, P, C.POINTER(hobo_batch_opts), P]
+    L.hobo_batch_launch_shape.argtypes = [P, I, C.POINTER(I), C.POINTER(I)]
+    for name in ("hobo_batch_create", "hobo_batch_layout", "hobo_batch_anneal", "hobo_batch_launch_shape"):
+        getattr(L, name).restype = I
     L.hobo_last_error.restype = C.c_char_p
     L.hobo_version.restype = C.c_char_p
     for name in ("hobo_create", "hobo_create_terms", "hobo_info", "hobo_energy", "hobo_energy_path",
@@ -249,3 +268,84 @@ class Instance:
 
 def version() -> str:
     return load_library().hobo_version().decode()
+
+
+def _event_handle(e):
+    if e is None:
+        return None
+    if not e.cuda_event:          # torch creates its events lazily
+        e.record()
+    return e.cuda_event
+
+
+class Batch:
+    """A batch plan over several instances (hobo_batch_create): instance t
+    contributes B[t] states; outputs are laid out instance after instance."""
+
+    def __init__(self, instances, B):
+        self.instances = list(instances)     # kept alive while the plan exists
+        self.B = [int(b) for b in B]
+        n = len(self.instances)
+        arr = (C.c_void_p * n)(*[i.handle.value for i in self.instances])
+        bs = np.ascontiguousarray(np.array(self.B, dtype=np.int32))
+        h = C.c_void_p()
+        _check(load_library().hobo_batch_create(C.byref(h), arr, n, bs.ctypes.data_as(C.c_void_p)))
+        self._h = h
+        so = np.zeros(n, np.int64)
+        wo = np.zeros(n, np.int64)
+        _check(load_library().hobo_batch_layout(self._h, so.ctypes.data_as(C.c_void_p), wo.ctypes.data_as(C.c_void_p)))
+        self.state_offset = so
+        self.word_offset = wo
+        self.total = int(sum(self.B))
+        self.words = int(sum(b * inst.W for b, inst in zip(self.B, self.instances)))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load_library().hobo_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def anneal(self, seeds, betas, *, mode: int = HOBO_BATCH_GRAPH, no_autotune: bool = False,
+               warps_per_cta: int = 0, ctas_per_sm: int = 0, want_final: bool = False,
+               want_accepts: bool = False, events=None, stream=None) -> dict:
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        seeds = np.ascontiguousarray(np.array(seeds, dtype=np.uint64))
+        betas = np.ascontiguousarray(betas, dtype=np.float32)
+        bestX = torch.zeros(self.words, dtype=torch.int32, device=dev)
+        bestE = torch.empty(self.total, dtype=torch.float64, device=dev)
+        X = torch.zeros(self.words, dtype=torch.int32, device=dev) if want_final else None
+        E = torch.empty(self.total, dtype=torch.float32, device=dev) if want_final else None
+        acc = torch.zeros(self.total, dtype=torch.int64, device=dev) if want_accepts else None
+        ev0, ev1 = (None, None) if events is None else (_event_handle(events[0]), _event_handle(events[1]))
+        o = hobo_batch_opts(mode, 1 if no_autotune else 0, warps_per_cta, ctas_per_sm, _ptr(acc), _ptr(X),
+                            _ptr(E), ev0, ev1)
+        _check(load_library().hobo_batch_anneal(self._h, seeds.ctypes.data_as(C.c_void_p),
+                                                betas.ctypes.data_as(C.c_void_p), betas.shape[0],
+                                                _ptr(bestX), _ptr(bestE), C.byref(o), _stream(stream)))
+        out = dict(bestX=bestX, bestE=bestE)
+        if X is not None:
+            out["X"], out["E"] = X, E
+        if acc is not None:
+            out["accepts"] = acc
+        return out
+
+    def rows(self, flat, t):
+        """View of instance t's block of a state-indexed or word-indexed output."""
+        inst = self.instances[t]
+        if flat.numel() == self.total:
+            o = int(self.state_offset[t])
+            return flat[o:o + self.B[t]]
+        o = int(self.word_offset[t])
+        return flat[o:o + self.B[t] * inst.W].view(self.B[t], inst.W)
+
+    def launch_shape(self, group: int = 0):
+        w = C.c_int()
+        c = C.c_int()
+        _check(load_library().hobo_batch_launch_shape(self._h, group, C.byref(w), C.byref(c)))
+        return w.value, c.value

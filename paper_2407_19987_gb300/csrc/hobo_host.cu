@@ -413,6 +413,21 @@ static int check_shape(int order, int N)
 
 using namespace hobo;
 
+int hobo::energy_dispatch(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g, bool flip,
+                          int path, cudaStream_t st)
+{
+    if (path == 2 || (path == 0 && h->dense)) {
+        cudaError_t e = launch_energy_tc(h, X, B, E, g, flip, st);
+        if (e == cudaSuccess) return HOBO_OK;
+        if (e != cudaErrorNotSupported) return cuda_fail(e, "tensor-core contraction");
+        if (path == 2) return fail(HOBO_ERR_UNSUPPORTED, "tensor-core path needs a dense order-3 instance");
+        (void)cudaGetLastError();
+    }
+    cudaError_t e = launch_energy_terms(h, X, B, E, g, flip, st);
+    if (e != cudaSuccess) return cuda_fail(e, "term-list contraction");
+    return HOBO_OK;
+}
+
 extern "C" {
 
 int hobo_create(hobo_h* out, const float* T, int order, int N, unsigned flags)
@@ -508,28 +523,13 @@ int hobo_info(hobo_h h, hobo_info_t* info)
     return HOBO_OK;
 }
 
-static int energy_impl(hobo_h h, const uint32_t* X, int B, float* E, float* g, bool flip, int path,
-                       cudaStream_t st)
-{
-    if (path == 2 || (path == 0 && h->dense)) {
-        cudaError_t e = launch_energy_tc(h, X, B, E, g, flip, st);
-        if (e == cudaSuccess) return HOBO_OK;
-        if (e != cudaErrorNotSupported) return cuda_fail(e, "tensor-core contraction");
-        if (path == 2) return fail(HOBO_ERR_UNSUPPORTED, "tensor-core path needs a dense order-3 instance");
-        (void)cudaGetLastError();
-    }
-    cudaError_t e = launch_energy_terms(h, X, B, E, g, flip, st);
-    if (e != cudaSuccess) return cuda_fail(e, "term-list contraction");
-    return HOBO_OK;
-}
-
 int hobo_energy_path(hobo_h h, const uint32_t* X, int B, float* E, float* dE, int path, void* stream)
 {
     if (!h) return fail(HOBO_ERR_ARG, "NULL instance");
     if (B < 0 || (B > 0 && (!X || !E))) return fail(HOBO_ERR_ARG, "bad X/E/B");
     if (path < 0 || path > 2) return fail(HOBO_ERR_ARG, "path must be 0, 1 or 2");
     if (B == 0) return HOBO_OK;
-    return energy_impl(h, X, B, E, dE, true, path, (cudaStream_t)stream);
+    return hobo::energy_dispatch(h, X, B, E, dE, true, path, (cudaStream_t)stream);
 }
 
 int hobo_energy(hobo_h h, const uint32_t* X, int B, float* E, float* dE, void* stream)
@@ -604,7 +604,7 @@ int hobo_anneal(hobo_h h, uint64_t seed, int B, const float* beta, int sweeps, u
 
     if (!o.resume) ACHECK(launch_init_states(d_X, B, N, W, seed, st), "init states");
     if (!(o.resume && o.g_io && o.E_io)) {
-        rc = energy_impl(h, d_X, B, d_E, d_g, false, 0, st);
+        rc = hobo::energy_dispatch(h, d_X, B, d_E, d_g, false, 0, st);
         if (rc != HOBO_OK) { cleanup(); return rc; }
     }
 

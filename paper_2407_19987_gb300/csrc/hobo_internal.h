@@ -116,4 +116,9 @@ cudaError_t make_tc_tensor_map(hobo_instance* h);
 
 void set_error(const std::string& msg);
 
+// Energy/field contraction with the automatic or explicit path (0 auto,
+// 1 term list, 2 tensor core); returns a HOBO_* status.
+int energy_dispatch(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g, bool flip,
+                    int path, cudaStream_t st);
+
 }  // namespace hobo

@@ -19,16 +19,7 @@ __global__ void init_states_kernel(uint32_t* __restrict__ X, int B, int N, int W
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= (int64_t)B * W) return;
     const int b = (int)(tid / W), w = (int)(tid % W);
-    uint32_t word = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const u32x4 r = philox10((uint32_t)(8 * w + q), 0u, (uint32_t)b, kStreamInit, k0, k1);
-        word |= ((r.a >> 31) << (4 * q)) | ((r.b >> 31) << (4 * q + 1)) |
-                ((r.c >> 31) << (4 * q + 2)) | ((r.d >> 31) << (4 * q + 3));
-    }
-    const int rem = N - 32 * w;
-    if (rem < 32) word &= (1u << rem) - 1u;
-    X[tid] = word;
+    X[tid] = init_word(b, w, N, k0, k1);
 }
 
 cudaError_t launch_init_states(uint32_t* X, int B, int N, int W, uint64_t seed, cudaStream_t st)
@@ -465,7 +456,7 @@ __global__ void sweep_plain_kernel(const SweepDev p)
     if (p.coef_bytes) p.coef_bytes[b] += nbytes;
 }
 
-static SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
+SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
 {
     SweepDev p{};
     p.N = h->N; p.W = h->W; p.B = a.B; p.sweeps = a.sweeps; p.sweep0 = a.sweep0;

@@ -192,19 +192,21 @@ __device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __res
     return bytes;
 }
 
-template <int WMAX, bool DENSE, int KU>
-__global__ void __launch_bounds__(kSweepWarps * 32, 4)
-sweep_tuned_kernel(const SweepDev p)
+// Shared-memory floats one warp needs for a state of N variables: fields,
+// bits and best bits, then the dense update's list of row offsets (read 8 at
+// a time); every part a multiple of 16 bytes.
+__host__ __device__ constexpr int warp_region_floats(int N, int WMAX)
 {
-    extern __shared__ float sm[];
+    return 2 * ((N + 3) & ~3) + 4 * (WMAX + 1) + 8;
+}
+
+// The whole anneal of state b of the instance described by p, run by one
+// warp whose shared-memory region starts at g.
+template <int WMAX, bool DENSE, int KU>
+__device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g, int lane)
+{
     const int N = p.N, W = p.W;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int b = blockIdx.x * kSweepWarps + warp;       // state of this warp
-    if (b >= p.B) return;                                // warp-uniform; no block barriers below
     const int NPAD = (N + 3) & ~3;
-    // per-warp region, every part a multiple of 16 bytes: fields, bits and
-    // best bits, then the dense update's list of row offsets (read 8 at a time)
-    float* g = sm + (size_t)warp * (2 * NPAD + 4 * (WMAX + 1) + 8);
     uint32_t* bs = reinterpret_cast<uint32_t*>(g + NPAD);   // bits + sentinel (sparse lookups)
     uint32_t* rows = bs + 4 * (WMAX + 1);                   // dense: offsets of the rows to read
 
@@ -309,10 +311,55 @@ sweep_tuned_kernel(const SweepDev p)
 }
 
 template <int WMAX, bool DENSE, int KU>
+__global__ void __launch_bounds__(kSweepWarps * 32, 4)
+sweep_tuned_kernel(const SweepDev p)
+{
+    extern __shared__ float sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x * kSweepWarps + warp;       // state of this warp
+    if (b >= p.B) return;                                // warp-uniform; no block barriers below
+    anneal_state<WMAX, DENSE, KU>(p, b, sm + (size_t)warp * warp_region_floats(p.N, WMAX), lane);
+}
+
+// Batched form: a persistent grid whose warps take (instance, state) work
+// items from a queue (items sorted by decreasing cost) until it is empty.
+// Every item is annealed exactly as the per-instance kernel would.
+template <int WMAX, bool DENSE, int KU>
+__global__ void __launch_bounds__(256)
+sweep_batch_kernel(const SweepDev* __restrict__ descs, const int2* __restrict__ items, int nitems,
+                   int* __restrict__ counter, int region_floats)
+{
+    extern __shared__ float sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* region = sm + (size_t)warp * region_floats;
+    while (true) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= nitems) break;
+        const int2 it = items[item];
+        anneal_state<WMAX, DENSE, KU>(descs[it.x], it.y, region, lane);
+        __syncwarp();
+    }
+}
+
+template <int WMAX, bool DENSE, int KU>
+inline cudaError_t run_batch(const SweepDev* descs, const int2* items, int nitems, int* counter, int Nmax,
+                             int warps, int ctas, cudaStream_t st)
+{
+    const int rf = warp_region_floats(Nmax, WMAX);
+    const size_t sm = sizeof(float) * (size_t)rf * warps;
+    auto kern = sweep_batch_kernel<WMAX, DENSE, KU>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<ctas, warps * 32, sm, st>>>(descs, items, nitems, counter, rf);
+    return cudaGetLastError();
+}
+
+template <int WMAX, bool DENSE, int KU>
 inline cudaError_t run_tuned(const SweepDev& p, cudaStream_t st)
 {
-    const int NPAD = (p.N + 3) & ~3;
-    const size_t per_warp = sizeof(float) * (size_t)(2 * NPAD + 4 * (WMAX + 1) + 8);
+    const size_t per_warp = sizeof(float) * (size_t)warp_region_floats(p.N, WMAX);
     const size_t sm = per_warp * kSweepWarps;
     auto kern = sweep_tuned_kernel<WMAX, DENSE, KU>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -323,6 +370,14 @@ inline cudaError_t run_tuned(const SweepDev& p, cudaStream_t st)
     return cudaGetLastError();
 }
 
+
+template <bool DENSE, int KU>
+cudaError_t dispatch_batch(const SweepDev* descs, const int2* items, int nitems, int* counter, int Nmax,
+                           int Wmax, int warps, int ctas, cudaStream_t st);
+template <> cudaError_t dispatch_batch<true, 1>(const SweepDev*, const int2*, int, int*, int, int, int, int, cudaStream_t);
+template <> cudaError_t dispatch_batch<false, 1>(const SweepDev*, const int2*, int, int*, int, int, int, int, cudaStream_t);
+template <> cudaError_t dispatch_batch<false, 2>(const SweepDev*, const int2*, int, int*, int, int, int, int, cudaStream_t);
+template <> cudaError_t dispatch_batch<false, 6>(const SweepDev*, const int2*, int, int*, int, int, int, int, cudaStream_t);
 
 template <bool DENSE, int KU>
 cudaError_t dispatch_tuned(const SweepDev& p, cudaStream_t st);

@@ -172,11 +172,10 @@ def random_sparse(seed: int, N: int, order: int, density: float, coef: str = "no
         total = math.comb(N, d)
         cnt = int(rng.binomial(total, density))
         rows.append(_sample_subsets(rng, N, d, cnt))
-    tuples = []
-    for r in rows:
-        for t in r:
-            tuples.append(pad_smallest(tuple(int(v) for v in t), order))
-    idx = np.array(tuples, dtype=np.int32).reshape(-1, order)
+    # pad each monomial with its smallest index in front (Sec. III.C)
+    padded = [np.concatenate([np.repeat(r[:, :1], order - r.shape[1], axis=1), r], axis=1)
+              for r in rows if r.shape[0] > 0]
+    idx = np.concatenate(padded, axis=0).astype(np.int32).reshape(-1, order)
     if coef == "normal":
         c = rng.standard_normal(idx.shape[0], dtype=np.float32)
         integer = False
