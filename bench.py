@@ -50,6 +50,7 @@ def parse():
                     help="run one small case of one kernel (for profilers) and exit")
     ap.add_argument("--case-states", type=int, default=4096)
     ap.add_argument("--case-sweeps", type=int, default=30)
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched-workload measurement")
     return ap.parse_args()
 
 
@@ -286,6 +287,8 @@ def run_ours(a):
     cl = cs.summary()
     if cl:
         line["clocks"] = cl
+    if rank == 0 and not a.no_extras:
+        line["extras"] = {"uneven_batch": measure_uneven_batch()}
     if rank == 0 and not a.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(inst, betas, a.cpu_states)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -296,6 +299,52 @@ def run_ours(a):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def measure_uneven_batch(plain_sample: int = 8):
+    """The batched form on the uneven workload: 512 order-3 instances,
+    N ~ U[16,192], 5% density, B=1024 states each, 500 sweeps.  Times one
+    graph replay of the whole batch, the per-instance tuned launches, and the
+    per-instance plain launches on the first `plain_sample` instances (scaled
+    to the batch by their share of attempted flips)."""
+    import torch
+
+    import paper_2407_19987_gb300 as H
+    insts = W.uneven_batch(4000, 512)
+    T0, T1, S, B = W.SCHEDULES["uneven_batch"]
+    betas = W.geometric_betas(T0, T1, S)
+    hs = [H.Instance.from_terms(i.idx, i.coef, i.N) for i in insts]
+    seeds = [4000 + t for t in range(len(hs))]
+    flips = sum(B * i.N * S for i in insts)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def timed(bt, mode, reps):
+        bt.anneal(seeds[:len(bt.B)], betas, mode=mode)          # warm-up (and autotune)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            bt.anneal(seeds[:len(bt.B)], betas, mode=mode, events=ev)
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        return statistics.mean(ms)
+
+    bt = H.Batch(hs, [B] * len(hs))
+    g_ms = timed(bt, H.HOBO_BATCH_GRAPH, 3)
+    t_ms = timed(bt, H.HOBO_BATCH_PER_INSTANCE_TUNED, 1)
+    sub = H.Batch(hs[:plain_sample], [B] * plain_sample)
+    p_ms_sub = timed(sub, H.HOBO_BATCH_PER_INSTANCE_PLAIN, 1)
+    sub_flips = sum(B * i.N * S for i in insts[:plain_sample])
+    p_rate = sub_flips / (p_ms_sub / 1000.0)
+    shape = bt.launch_shape(0)
+    return {"workload": "uneven_batch: 512 order-3 instances, N~U[16,192], 5% density, N(0,1), "
+                        "B=1024 each, 500 sweeps, T 5->0.02",
+            "attempted_flips": flips,
+            "graph_ms": g_ms, "graph_flips_per_s": flips / (g_ms / 1000.0),
+            "per_instance_tuned_ms": t_ms, "per_instance_tuned_flips_per_s": flips / (t_ms / 1000.0),
+            "per_instance_plain_flips_per_s": p_rate,
+            "per_instance_plain_sample": f"first {plain_sample} instances ({sub_flips} flips, {p_ms_sub:.1f} ms)",
+            "speedup_graph_vs_plain": (flips / (g_ms / 1000.0)) / p_rate,
+            "autotuned_shape": {"warps_per_cta": shape[0], "ctas": shape[1]}}
 
 
 def run_kernel_case(a):

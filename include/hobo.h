@@ -284,6 +284,77 @@ int hobo_batch_anneal(hobo_batch_h bh, const uint64_t* seeds, const float* beta,
  * sparse order <= 3, order 4, order 5..8, skipping empty groups). */
 int hobo_batch_launch_shape(hobo_batch_h bh, int group, int* warps_per_cta, int* ctas);
 
+/* ---- learned flip proposal -------------------------------------------- */
+
+/*
+ * A small MLP scores each bit of a state from three features (no
+ * counterpart in the paper; it is the learned part of the tuned annealer):
+ *   f0 = clamp(beta * g_i, -vmax, vmax) / 8,  f1 = 2 x_i - 1,  f2 = -ln(beta) / 4
+ * with g_i the bit's local field.  Network: 3 -> H -> H -> 1 (ReLU hidden
+ * layers, logit output), bf16 weights, float32 sums; trained with binary
+ * cross-entropy and Adam by the library's own kernels.  Flat parameter
+ * layout (H = hidden): W1 [H][3] | b1 [H] | W2 [H][H] (row = output unit) |
+ * b2 [H] | w3 [H] | b3.  All device pointers are on the current device.
+ */
+typedef struct hobo_mlp* hobo_mlp_h;
+
+/* Create a network of hidden width H (multiple of 32, 32..1024) with He
+ * initialisation from `seed`. */
+int hobo_mlp_create(hobo_mlp_h* out, int hidden, uint64_t seed);
+void hobo_mlp_destroy(hobo_mlp_h m);
+int64_t hobo_mlp_num_params(hobo_mlp_h m);
+/* Copy the parameters to host (rounded = 1: the bf16-rounded values the
+ * passes use; 0: the float32 optimiser masters). */
+int hobo_mlp_get(hobo_mlp_h m, float* host, int rounded);
+/* Set the parameters from host float32 values (also resets Adam). */
+int hobo_mlp_set(hobo_mlp_h m, const float* host);
+/* Logits of n feature rows F (device [n][3]) into logit (device [n]). */
+int hobo_mlp_forward(hobo_mlp_h m, const float* F, int64_t n, float* logit, void* stream);
+/* Mean binary cross-entropy of rows F against labels y (device [n], 0/1)
+ * and its gradient w.r.t. the bf16-rounded parameters: grad device
+ * [num_params] or NULL, loss device [1] or NULL. */
+int hobo_mlp_loss_grad(hobo_mlp_h m, const float* F, const float* y, int64_t n, float* grad, float* loss,
+                       void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on a mini-batch. */
+int hobo_mlp_train_step(hobo_mlp_h m, const float* F, const float* y, int64_t n, float lr, float* loss,
+                        void* stream);
+/* Checkpoint: one JSON header line, then the bf16 parameters. */
+int hobo_mlp_save(hobo_mlp_h m, const char* path);
+int hobo_mlp_load(hobo_mlp_h* out, const char* path);
+
+typedef struct {
+    int plain_every;     /* every plain_every-th sweep is plain (default 4);
+                            <= 1: all sweeps plain (network unused) */
+    float top_frac;      /* learned sweeps attempt the top ceil(top_frac*N)
+                            bits by score (0 = 1.0: all bits) */
+    int table_size;      /* grid points of the per-sweep score table (0 = 1024) */
+    float vmax;          /* clamp of beta*g in the features (0 = 32) */
+    int rec_every;       /* record sweeps s with s % rec_every == 0 (0: none) */
+    int rec_states;      /* ... for states b < rec_states */
+    float* rec_F;        /* device [ceil(sweeps/rec_every)][rec_states][N][3]: features */
+    float* rec_y;        /* device [..][rec_states][N]: label 1 if the bit then
+                            differs from the state's final best state, else 0 */
+    uint32_t* X_out;     /* device [B][W] or NULL: final states */
+    float* E_out;        /* device [B] or NULL: final float32 energies */
+    int64_t* accepts;    /* device [B] or NULL: accepted flips (added to) */
+    void* ev_begin;      /* cudaEvent_t or NULL: recorded before the work */
+    void* ev_end;        /* cudaEvent_t or NULL: recorded after the work */
+} hobo_learned_opts;
+
+/*
+ * hobo_anneal_learned -- hobo_anneal with the learned proposal: in learned
+ * sweeps each state attempts its bits in descending network score (ties by
+ * index), the top ceil(top_frac*N) of them, with the unchanged Metropolis
+ * test and random words; every plain_every-th sweep is the plain sweep
+ * over all bits in order, which stays the fallback.  Scores come from a
+ * per-sweep table of the network over (clamped beta*g, bit), evaluated by
+ * the library's forward kernel and read with linear interpolation.  m may
+ * be NULL (all sweeps plain).  Requires N <= 256.  Same seed, beta, outputs
+ * and errors as hobo_anneal; with all sweeps plain the results equal it.
+ */
+int hobo_anneal_learned(hobo_h h, hobo_mlp_h m, uint64_t seed, int B, const float* beta, int sweeps,
+                        uint32_t* bestX, double* bestE, const hobo_learned_opts* opts, void* stream);
+
 /* Human-readable message of the last error on this thread ("" if none). */
 const char* hobo_last_error(void);
 

@@ -27,6 +27,14 @@
  *                         brute-forced instances.  The acceptance rule and
  *                         the random-number layout are readings (the paper
  *                         names simulated annealing only, Sec. II.D.1).
+ *   orc_mlp_forward,      pinned: finite differences of the loss, networks
+ *   orc_mlp_loss_grad     built to compute a known function, closed forms
+ *                         of the loss at constant logits
+ *   orc_anneal_learned    pinned: equals orc_anneal without a network and
+ *                         with a constant network (ties by index); the set
+ *                         of bits a learned sweep attempts equals the top
+ *                         scores of the sweep's start state.  The proposal
+ *                         itself has no counterpart in the paper.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -363,4 +371,207 @@ void orc_anneal_naive(const int32_t* idx, const double* coef, int64_t nnz, int o
         accepts[bb] = acc;
     }
     free(x);
+}
+
+/* ------------------------------------------------------------------ */
+/* Learned flip proposal: a small MLP scoring each bit from three        */
+/* inputs (scaled local field, bit, temperature).  No counterpart in the */
+/* paper; the architecture is 3 -> H -> H -> 1 with ReLU hidden layers, */
+/* a logit output and binary cross-entropy against a 0/1 label:          */
+/*   z1 = W1 f + b1, h1 = max(z1, 0)                                     */
+/*   z2 = W2 h1 + b2, h2 = max(z2, 0)                                    */
+/*   logit = w3 . h2 + b3                                                */
+/*   loss = mean over rows of softplus(logit) - y * logit                */
+/* Row-major weights: W1 [H][3], W2 [H][H] (row = output unit).          */
+/* Gradients are of the mean loss, by the chain rule, in float64.        */
+/* ------------------------------------------------------------------ */
+
+static double relu(double v) { return v > 0.0 ? v : 0.0; }
+
+static double softplus(double v)
+{
+    return v > 0.0 ? v + log1p(exp(-v)) : log1p(exp(v));
+}
+
+void orc_mlp_forward(int H, const double* W1, const double* b1, const double* W2, const double* b2,
+                     const double* w3, double b3, const double* F, int64_t n, double* logit)
+{
+    double* h1 = (double*)malloc((size_t)H * sizeof(double));
+    for (int64_t r = 0; r < n; ++r) {
+        const double* f = F + r * 3;
+        for (int u = 0; u < H; ++u)
+            h1[u] = relu(W1[u * 3 + 0] * f[0] + W1[u * 3 + 1] * f[1] + W1[u * 3 + 2] * f[2] + b1[u]);
+        double out = b3;
+        for (int v = 0; v < H; ++v) {
+            double z = b2[v];
+            for (int u = 0; u < H; ++u) z += W2[(int64_t)v * H + u] * h1[u];
+            out += w3[v] * relu(z);
+        }
+        logit[r] = out;
+    }
+    free(h1);
+}
+
+double orc_mlp_loss_grad(int H, const double* W1, const double* b1, const double* W2, const double* b2,
+                         const double* w3, double b3, const double* F, const double* y, int64_t n,
+                         double* gW1, double* gb1, double* gW2, double* gb2, double* gw3, double* gb3)
+{
+    double* z1 = (double*)malloc((size_t)H * sizeof(double));
+    double* h1 = (double*)malloc((size_t)H * sizeof(double));
+    double* z2 = (double*)malloc((size_t)H * sizeof(double));
+    double* h2 = (double*)malloc((size_t)H * sizeof(double));
+    double* d2 = (double*)malloc((size_t)H * sizeof(double));
+    double* d1 = (double*)malloc((size_t)H * sizeof(double));
+    memset(gW1, 0, sizeof(double) * (size_t)H * 3);
+    memset(gb1, 0, sizeof(double) * (size_t)H);
+    memset(gW2, 0, sizeof(double) * (size_t)H * H);
+    memset(gb2, 0, sizeof(double) * (size_t)H);
+    memset(gw3, 0, sizeof(double) * (size_t)H);
+    *gb3 = 0.0;
+    double loss = 0.0;
+    for (int64_t r = 0; r < n; ++r) {
+        const double* f = F + r * 3;
+        for (int u = 0; u < H; ++u) {
+            z1[u] = W1[u * 3 + 0] * f[0] + W1[u * 3 + 1] * f[1] + W1[u * 3 + 2] * f[2] + b1[u];
+            h1[u] = relu(z1[u]);
+        }
+        double out = b3;
+        for (int v = 0; v < H; ++v) {
+            double z = b2[v];
+            for (int u = 0; u < H; ++u) z += W2[(int64_t)v * H + u] * h1[u];
+            z2[v] = z;
+            h2[v] = relu(z);
+            out += w3[v] * h2[v];
+        }
+        loss += softplus(out) - y[r] * out;
+        /* d loss / d logit = sigmoid(logit) - y, divided by n for the mean */
+        const double dl = (1.0 / (1.0 + exp(-out)) - y[r]) / (double)n;
+        *gb3 += dl;
+        for (int v = 0; v < H; ++v) {
+            gw3[v] += dl * h2[v];
+            d2[v] = z2[v] > 0.0 ? dl * w3[v] : 0.0;
+            gb2[v] += d2[v];
+        }
+        for (int u = 0; u < H; ++u) d1[u] = 0.0;
+        for (int v = 0; v < H; ++v) {
+            if (d2[v] == 0.0) continue;
+            for (int u = 0; u < H; ++u) {
+                gW2[(int64_t)v * H + u] += d2[v] * h1[u];
+                d1[u] += d2[v] * W2[(int64_t)v * H + u];
+            }
+        }
+        for (int u = 0; u < H; ++u) {
+            const double d = z1[u] > 0.0 ? d1[u] : 0.0;
+            gW1[u * 3 + 0] += d * f[0];
+            gW1[u * 3 + 1] += d * f[1];
+            gW1[u * 3 + 2] += d * f[2];
+            gb1[u] += d;
+        }
+    }
+    free(z1); free(h1); free(z2); free(h2); free(d2); free(d1);
+    return loss / (double)n;
+}
+
+/* ------------------------------------------------------------------ */
+/* Annealing with the learned proposal (no counterpart in the paper).    */
+/* Sweep s is plain (bits 0..N-1 in order, as orc_anneal) when there is  */
+/* no network, when plain_every <= 1, or when s % plain_every ==         */
+/* plain_every - 1.  Otherwise, at the start of the sweep every bit i is */
+/* scored by the network on its features                                 */
+/*   f0 = clamp(beta_s * g_i, -vmax, vmax) / 8                           */
+/*   f1 = 2 x_i - 1,  f2 = -ln(beta_s) / 4                               */
+/* (f0 in float32 from the float32 field, f1 exact, f2 in float64), the  */
+/* bits are ordered by descending score with ties broken by ascending    */
+/* index, and the first max(1, ceil(top_frac * N)) of them are attempted */
+/* in that order with the same Metropolis test and random word (bit i,  */
+/* sweep s) as a plain sweep.                                            */
+/* Recording: for states b < rec_B and sweeps with s % rec_every == 0,   */
+/* row (s / rec_every, b, i) gets the features of bit i at its decision  */
+/* and its bit then (rec_x); rows of bits not attempted are left alone.  */
+/* ------------------------------------------------------------------ */
+
+typedef struct { double score; int i; } scored_t;
+
+static int by_score_desc(const void* pa, const void* pb)
+{
+    const scored_t* a = (const scored_t*)pa;
+    const scored_t* b = (const scored_t*)pb;
+    if (a->score > b->score) return -1;
+    if (a->score < b->score) return 1;
+    return (a->i > b->i) - (a->i < b->i);
+}
+
+static float clampf_(float v, float lo, float hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+void orc_anneal_learned(const int32_t* idx, const double* coef, int64_t nnz, int order, int N,
+                        uint64_t seed, int64_t B, const float* betas, int sweeps,
+                        int H, const double* W1, const double* b1, const double* W2, const double* b2,
+                        const double* w3, double b3, int plain_every, float top_frac, float vmax,
+                        uint8_t* Xfinal, double* Efinal, uint8_t* Xbest, double* Ebest, int64_t* accepts,
+                        int rec_every, int64_t rec_B, float* rec_F, uint8_t* rec_x)
+{
+    incidence_t inc = build_incidence(idx, nnz, order, N);
+    uint8_t* x = (uint8_t*)malloc((size_t)N);
+    double* g = (double*)malloc((size_t)N * sizeof(double));
+    double* F = (double*)malloc((size_t)N * 3 * sizeof(double));
+    double* sc = (double*)malloc((size_t)N * sizeof(double));
+    scored_t* ord = (scored_t*)malloc((size_t)N * sizeof(scored_t));
+    const int learned = W1 != NULL && plain_every > 1;
+    for (int64_t b = 0; b < B; ++b) {
+        for (int i = 0; i < N; ++i)
+            x[i] = (uint8_t)(philox_word(seed, (uint32_t)i, 0u, (uint32_t)b, 1u) >> 31);
+        orc_fields(idx, coef, nnz, order, N, x, g);
+        double E = orc_energy(idx, coef, nnz, order, x);
+        double Eb = E;
+        memcpy(Xbest + b * N, x, (size_t)N);
+        int64_t acc = 0;
+        for (int s = 0; s < sweeps; ++s) {
+            const float beta = betas[s];
+            const double f2 = -log((double)beta) / 4.0;
+            const int plain = !learned || (s % plain_every) == plain_every - 1;
+            int nvisit = N;
+            if (!plain) {
+                for (int i = 0; i < N; ++i) {
+                    float gi = (float)g[i];
+                    float v = clampf_(beta * gi, -vmax, vmax);
+                    F[i * 3 + 0] = (double)(v / 8.0f);
+                    F[i * 3 + 1] = x[i] ? 1.0 : -1.0;
+                    F[i * 3 + 2] = f2;
+                }
+                orc_mlp_forward(H, W1, b1, W2, b2, w3, b3, F, N, sc);
+                for (int i = 0; i < N; ++i) { ord[i].score = sc[i]; ord[i].i = i; }
+                qsort(ord, (size_t)N, sizeof(scored_t), by_score_desc);
+                float want = top_frac * (float)N;
+                nvisit = (int)ceilf(want);
+                if (nvisit > N) nvisit = N;
+                if (nvisit < 1) nvisit = 1;
+            }
+            const int rec = rec_F && b < rec_B && (s % rec_every) == 0;
+            const int64_t rbase = rec ? ((int64_t)(s / rec_every) * rec_B + b) * N : 0;
+            for (int k = 0; k < nvisit; ++k) {
+                const int i = plain ? k : ord[k].i;
+                float gi = (float)g[i];
+                float dE = x[i] ? -gi : gi;
+                if (rec) {
+                    float v = clampf_(beta * gi, -vmax, vmax);
+                    rec_F[(rbase + i) * 3 + 0] = v / 8.0f;
+                    rec_F[(rbase + i) * 3 + 1] = x[i] ? 1.0f : -1.0f;
+                    rec_F[(rbase + i) * 3 + 2] = (float)f2;
+                    rec_x[rbase + i] = x[i];
+                }
+                uint32_t w = philox_word(seed, (uint32_t)i, (uint32_t)s, (uint32_t)b, 0u);
+                if (orc_metropolis(dE, beta, w)) {
+                    E += (x[i] ? -g[i] : g[i]);
+                    apply_flip(idx, coef, order, &inc, x, g, i);
+                    acc++;
+                    if (E < Eb) { Eb = E; memcpy(Xbest + b * N, x, (size_t)N); }
+                }
+            }
+        }
+        memcpy(Xfinal + b * N, x, (size_t)N);
+        Efinal[b] = E;
+        Ebest[b] = Eb;
+        accepts[b] = acc;
+    }
+    free(ord); free(sc); free(F); free(g); free(x); free(inc.start); free(inc.list);
 }

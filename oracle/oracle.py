@@ -55,6 +55,12 @@ def lib():
                                     P, P, P, P, P, i64, P]
         _lib.orc_anneal_naive.argtypes = [P, P, i64, i32, i32, u64, i64, i64, P, i32,
                                           P, P, P, P, P]
+        _lib.orc_anneal_learned.argtypes = [P, P, i64, i32, i32, u64, i64, P, i32,
+                                            i32, P, P, P, P, P, dbl, i32, flt, flt,
+                                            P, P, P, P, P, i32, i64, P, P]
+        _lib.orc_mlp_forward.argtypes = [i32, P, P, P, P, P, dbl, P, i64, P]
+        _lib.orc_mlp_loss_grad.restype = dbl
+        _lib.orc_mlp_loss_grad.argtypes = [i32, P, P, P, P, P, dbl, P, P, i64, P, P, P, P, P, P]
     return _lib
 
 
@@ -158,3 +164,72 @@ def anneal(inst, seed: int, B: int, betas: np.ndarray, state0: int = 0, rec_B: i
                      _p(betas), S, _p(Xf), _p(Ef), _p(Xb), _p(Eb), _p(acc), rec_B,
                      _p(rec) if rec is not None else None)
     return dict(X=Xf, E=Ef, bestX=Xb, bestE=Eb, accepts=acc, rec=rec)
+
+
+def _mlp_args(w):
+    H = w["b1"].shape[0]
+    arrs = [np.ascontiguousarray(w[k], dtype=np.float64) for k in ("W1", "b1", "W2", "b2", "w3")]
+    return H, arrs, float(np.asarray(w["b3"]).reshape(-1)[0])
+
+
+def mlp_forward(w: dict, F: np.ndarray) -> np.ndarray:
+    """Logits of the MLP (weights dict W1 [H,3], b1, W2 [H,H], b2, w3, b3) on rows F [n,3]."""
+    H, (W1, b1, W2, b2, w3), b3 = _mlp_args(w)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    out = np.zeros(F.shape[0], np.float64)
+    lib().orc_mlp_forward(H, _p(W1), _p(b1), _p(W2), _p(b2), _p(w3), b3, _p(F), F.shape[0], _p(out))
+    return out
+
+
+def mlp_loss_grad(w: dict, F: np.ndarray, y: np.ndarray):
+    """Mean binary cross-entropy and its gradients (dict like w)."""
+    H, (W1, b1, W2, b2, w3), b3 = _mlp_args(w)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    g = {"W1": np.zeros((H, 3)), "b1": np.zeros(H), "W2": np.zeros((H, H)), "b2": np.zeros(H),
+         "w3": np.zeros(H)}
+    gb3 = np.zeros(1)
+    loss = lib().orc_mlp_loss_grad(H, _p(W1), _p(b1), _p(W2), _p(b2), _p(w3), b3, _p(F), _p(y), F.shape[0],
+                                   _p(g["W1"]), _p(g["b1"]), _p(g["W2"]), _p(g["b2"]), _p(g["w3"]), _p(gb3))
+    g["b3"] = gb3
+    return loss, g
+
+
+def anneal_learned(inst, seed: int, B: int, betas: np.ndarray, w: dict | None, plain_every: int = 4,
+                   top_frac: float = 1.0, vmax: float = 32.0, rec_every: int = 0, rec_B: int = 0) -> dict:
+    """Oracle annealer with the learned proposal (network weights ``w`` as
+    in mlp_forward, or None for plain sweeps only).  With recording, returns
+    rec_F [rows, 3], rec_x (0xFF where a bit was not attempted) and the
+    labels rec_y: 1 if the recorded bit differs from the state's final best
+    bit, 0 if not, -1 if not attempted."""
+    idx, coef = _terms(inst)
+    betas = np.ascontiguousarray(betas, dtype=np.float32)
+    S = betas.shape[0]
+    N = inst.N
+    Xf = np.zeros((B, N), np.uint8)
+    Xb = np.zeros((B, N), np.uint8)
+    Ef = np.zeros(B, np.float64)
+    Eb = np.zeros(B, np.float64)
+    acc = np.zeros(B, np.int64)
+    if w is not None:
+        H, (W1, b1, W2, b2, w3), b3 = _mlp_args(w)
+        wp = [_p(a) for a in (W1, b1, W2, b2, w3)]
+    else:
+        H, wp, b3 = 0, [None] * 5, 0.0
+    rec = rec_every > 0 and rec_B > 0
+    rB = min(rec_B, B) if rec else 0
+    nrows = ((S + rec_every - 1) // rec_every) * rB * N if rec else 0
+    recF = np.zeros((max(nrows, 1), 3), np.float32)
+    recx = np.full(max(nrows, 1), 0xFF, np.uint8)
+    lib().orc_anneal_learned(_p(idx), _p(coef), idx.shape[0], inst.order, N, seed, B, _p(betas), S,
+                             H, *wp, b3, plain_every, float(top_frac), float(vmax),
+                             _p(Xf), _p(Ef), _p(Xb), _p(Eb), _p(acc),
+                             max(rec_every, 1), rB, _p(recF) if rec else None, _p(recx) if rec else None)
+    out = dict(X=Xf, E=Ef, bestX=Xb, bestE=Eb, accepts=acc)
+    if rec:
+        recF, recx = recF[:nrows], recx[:nrows]
+        b_of_row = (np.arange(nrows) // N) % rB
+        best = Xb[b_of_row, np.arange(nrows) % N]
+        y = np.where(recx == 0xFF, -1.0, (recx != best).astype(np.float64)).astype(np.float32)
+        out.update(rec_F=recF, rec_x=recx, rec_y=y)
+    return out

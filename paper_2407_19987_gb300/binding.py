@@ -62,6 +62,13 @@ class hobo_batch_opts(C.Structure):
                 ("E_out", C.c_void_p), ("ev_begin", C.c_void_p), ("ev_end", C.c_void_p)]
 
 
+class hobo_learned_opts(C.Structure):
+    _fields_ = [("plain_every", C.c_int), ("top_frac", C.c_float), ("table_size", C.c_int),
+                ("vmax", C.c_float), ("rec_every", C.c_int), ("rec_states", C.c_int),
+                ("rec_F", C.c_void_p), ("rec_y", C.c_void_p), ("X_out", C.c_void_p), ("E_out", C.c_void_p),
+                ("accepts", C.c_void_p), ("ev_begin", C.c_void_p), ("ev_end", C.c_void_p)]
+
+
 class hobo_anneal_opts(C.Structure):
     _fields_ = [("mode", C.c_int), ("states_per_block", C.c_int), ("sweep0", C.c_int),
                 ("resume", C.c_int), ("X_io", C.c_void_p), ("bestE32_io", C.c_void_p),
@@ -100,6 +107,22 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     L.hobo_batch_anneal.argtypes = [P, P, P, I, P, P, C.POINTER(hobo_batch_opts), P]
     L.hobo_batch_launch_shape.argtypes = [P, I, C.POINTER(I), C.POINTER(I)]
     for name in ("hobo_batch_create", "hobo_batch_layout", "hobo_batch_anneal", "hobo_batch_launch_shape"):
+        getattr(L, name).restype = I
+    L.hobo_mlp_create.argtypes = [C.POINTER(P), I, U64]
+    L.hobo_mlp_destroy.argtypes = [P]
+    L.hobo_mlp_destroy.restype = None
+    L.hobo_mlp_num_params.argtypes = [P]
+    L.hobo_mlp_num_params.restype = I64
+    L.hobo_mlp_get.argtypes = [P, P, I]
+    L.hobo_mlp_set.argtypes = [P, P]
+    L.hobo_mlp_forward.argtypes = [P, P, I64, P, P]
+    L.hobo_mlp_loss_grad.argtypes = [P, P, P, I64, P, P, P]
+    L.hobo_mlp_train_step.argtypes = [P, P, P, I64, C.c_float, P, P]
+    L.hobo_mlp_save.argtypes = [P, C.c_char_p]
+    L.hobo_mlp_load.argtypes = [C.POINTER(P), C.c_char_p]
+    L.hobo_anneal_learned.argtypes = [P, P, U64, I, P, I, P, P, C.POINTER(hobo_learned_opts), P]
+    for name in ("hobo_mlp_create", "hobo_mlp_get", "hobo_mlp_set", "hobo_mlp_forward", "hobo_mlp_loss_grad",
+                 "hobo_mlp_train_step", "hobo_mlp_save", "hobo_mlp_load", "hobo_anneal_learned"):
         getattr(L, name).restype = I
     L.hobo_last_error.restype = C.c_char_p
     L.hobo_version.restype = C.c_char_p
@@ -349,3 +372,116 @@ class Batch:
         c = C.c_int()
         _check(load_library().hobo_batch_launch_shape(self._h, group, C.byref(w), C.byref(c)))
         return w.value, c.value
+
+
+class MLP:
+    """The learned flip-proposal network (hobo_mlp_*): 3 -> H -> H -> 1,
+    bf16 weights, trained by the library's kernels."""
+
+    def __init__(self, hidden: int = 256, seed: int = 0, _handle=None):
+        if _handle is None:
+            h = C.c_void_p()
+            _check(load_library().hobo_mlp_create(C.byref(h), hidden, C.c_uint64(seed)))
+            _handle = h
+        self._h = _handle
+        self.nparam = int(load_library().hobo_mlp_num_params(self._h))
+        self.hidden = hidden
+
+    @classmethod
+    def load(cls, path: str) -> "MLP":
+        h = C.c_void_p()
+        _check(load_library().hobo_mlp_load(C.byref(h), path.encode()))
+        m = cls(_handle=h)
+        m.hidden = (int(np.sqrt(36 + 4 * (m.nparam - 1))) - 6) // 2
+        return m
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load_library().hobo_mlp_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def params(self, rounded: bool = True) -> np.ndarray:
+        out = np.zeros(self.nparam, np.float32)
+        _check(load_library().hobo_mlp_get(self._h, out.ctypes.data_as(C.c_void_p), 1 if rounded else 0))
+        return out
+
+    def set_params(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(load_library().hobo_mlp_set(self._h, flat.ctypes.data_as(C.c_void_p)))
+
+    def unpack(self, flat: np.ndarray) -> dict:
+        H = self.hidden
+        o = 0
+        out = {}
+        for k, shape in (("W1", (H, 3)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("w3", (H,)), ("b3", (1,))):
+            n = int(np.prod(shape))
+            out[k] = np.asarray(flat[o:o + n], dtype=np.float64).reshape(shape)
+            o += n
+        return out
+
+    def forward(self, F, stream=None):
+        import torch
+        logit = torch.empty(F.shape[0], dtype=torch.float32, device=F.device)
+        _check(load_library().hobo_mlp_forward(self._h, _ptr(F), F.shape[0], _ptr(logit), _stream(stream)))
+        return logit
+
+    def loss_grad(self, F, y, stream=None):
+        import torch
+        g = torch.empty(self.nparam, dtype=torch.float32, device=F.device)
+        loss = torch.empty(1, dtype=torch.float32, device=F.device)
+        _check(load_library().hobo_mlp_loss_grad(self._h, _ptr(F), _ptr(y), F.shape[0], _ptr(g), _ptr(loss),
+                                                 _stream(stream)))
+        return loss, g
+
+    def train_step(self, F, y, lr: float, loss=None, stream=None):
+        _check(load_library().hobo_mlp_train_step(self._h, _ptr(F), _ptr(y), F.shape[0], C.c_float(lr),
+                                                  _ptr(loss), _stream(stream)))
+
+    def save(self, path: str):
+        _check(load_library().hobo_mlp_save(self._h, path.encode()))
+
+
+def anneal_learned(inst: Instance, mlp, seed: int, B: int, betas: np.ndarray, *, plain_every: int = 4,
+                   top_frac: float = 1.0, table_size: int = 0, vmax: float = 0.0, rec_every: int = 0,
+                   rec_states: int = 0, want_final: bool = False, want_accepts: bool = False, events=None,
+                   stream=None) -> dict:
+    """hobo_anneal_learned through the C ABI; returns CUDA tensors."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    betas = np.ascontiguousarray(betas, dtype=np.float32)
+    S = betas.shape[0]
+    bestX = torch.zeros((B, inst.W), dtype=torch.int32, device=dev)
+    bestE = torch.empty(B, dtype=torch.float64, device=dev)
+    X = torch.zeros((B, inst.W), dtype=torch.int32, device=dev) if want_final else None
+    E = torch.empty(B, dtype=torch.float32, device=dev) if want_final else None
+    acc = torch.zeros(B, dtype=torch.int64, device=dev) if want_accepts else None
+    recF = recy = None
+    if rec_every > 0 and rec_states > 0:
+        nr = ((S + rec_every - 1) // rec_every) * min(rec_states, B) * inst.N
+        recF = torch.zeros((nr, 3), dtype=torch.float32, device=dev)
+        recy = torch.zeros(nr, dtype=torch.float32, device=dev)
+    ev0, ev1 = (None, None) if events is None else (_event_handle(events[0]), _event_handle(events[1]))
+    o = hobo_learned_opts(plain_every, top_frac, table_size, vmax, rec_every, rec_states, _ptr(recF), _ptr(recy),
+                          _ptr(X), _ptr(E), _ptr(acc), ev0, ev1)
+    _check(load_library().hobo_anneal_learned(inst.handle, None if mlp is None else mlp.handle,
+                                              C.c_uint64(seed & (2 ** 64 - 1)), B,
+                                              betas.ctypes.data_as(C.c_void_p), S, _ptr(bestX), _ptr(bestE),
+                                              C.byref(o), _stream(stream)))
+    out = dict(bestX=bestX, bestE=bestE)
+    if X is not None:
+        out["X"], out["E"] = X, E
+    if acc is not None:
+        out["accepts"] = acc
+    if recF is not None:
+        out["rec_F"], out["rec_y"] = recF, recy
+    return out

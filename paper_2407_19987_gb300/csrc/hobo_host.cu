@@ -92,8 +92,8 @@ static int upload(T** dst, const std::vector<T>& src)
 
 static void free_layouts(DevLayouts& d)
 {
-    void* ptrs[] = {d.tvars, d.tcoef32, d.tcoef64, d.tfix, d.fptr, d.fvars, d.fcoef, d.bptr, d.rtgt,
-                    d.rbeg, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf,
+    void* ptrs[] = {d.tvars, d.tcoef32, d.tcoef64, d.tfix, d.fptr, d.fvars, d.fcoef, d.cptr, d.chdr,
+                    d.ltgt, d.lcnt, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf,
                     d.C3fix, d.S2fix, d.afix, d.pair_m, d.pair_j};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -342,10 +342,46 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
         }
         d.R = (int64_t)rtgt.size();
         d.U = U;
-        if (rtgt.empty()) rtgt.push_back(0);
+        // Sliced ELL: the target records of bit i in chunks of 32 (lane =
+        // record); entry k of lane l of a chunk at offset + 32 k + l, padded
+        // to the chunk's longest record with zero coefficients.
+        std::vector<int32_t> cptr((size_t)N + 1, 0);
+        std::vector<int2> chdr;
+        std::vector<uint16_t> ltgt, lcnt;
+        std::vector<float> ec;
+        std::vector<uint16_t> econd;
+        int64_t eoff = 0;
+        for (int i = 0; i < N; ++i) {
+            cptr[i] = (int32_t)chdr.size();
+            for (int r0 = bptr[i]; r0 < bptr[i + 1]; r0 += 32) {
+                const int nrec = std::min(32, bptr[i + 1] - r0);
+                int K = 0;
+                for (int l = 0; l < nrec; ++l) K = std::max(K, rbeg[r0 + l + 1] - rbeg[r0 + l]);
+                chdr.push_back(make_int2((int)eoff, K * 64 + nrec));
+                for (int l = 0; l < 32; ++l) {
+                    ltgt.push_back(l < nrec ? (uint16_t)rtgt[r0 + l] : (uint16_t)0);
+                    lcnt.push_back(l < nrec ? (uint16_t)(rbeg[r0 + l + 1] - rbeg[r0 + l]) : (uint16_t)0);
+                }
+                ec.resize((size_t)(eoff + 32LL * K), 0.0f);
+                econd.resize((size_t)(eoff + 32LL * K) * KU, (uint16_t)N);
+                for (int l = 0; l < nrec; ++l)
+                    for (int k = 0; k < rbeg[r0 + l + 1] - rbeg[r0 + l]; ++k) {
+                        const int64_t src = rbeg[r0 + l] + k, dst = eoff + 32LL * k + l;
+                        ec[dst] = uc[src];
+                        for (int q = 0; q < KU; ++q) econd[dst * KU + q] = ucond[src * KU + q];
+                    }
+                eoff += 32LL * K;
+                if (eoff >= (int64_t)INT32_MAX) return fail(HOBO_ERR_UNSUPPORTED, "update list too large");
+            }
+        }
+        cptr[N] = (int32_t)chdr.size();
+        if (chdr.empty()) { chdr.push_back(make_int2(0, 0)); ltgt.assign(32, 0); lcnt.assign(32, 0); }
+        if (ec.empty()) { ec.push_back(0.0f); econd.assign(KU, (uint16_t)N); }
+        d.C = (int64_t)chdr.size();
+        d.Epad = eoff;
         int rc;
-        if ((rc = upload(&d.bptr, bptr)) || (rc = upload(&d.rtgt, rtgt)) || (rc = upload(&d.rbeg, rbeg)) ||
-            (rc = upload(&d.ucoef, uc)) || (rc = upload(&d.uconds, ucond)))
+        if ((rc = upload(&d.cptr, cptr)) || (rc = upload(&d.chdr, chdr)) || (rc = upload(&d.ltgt, ltgt)) ||
+            (rc = upload(&d.lcnt, lcnt)) || (rc = upload(&d.ucoef, ec)) || (rc = upload(&d.uconds, econd)))
             return rc;
     }
     return HOBO_OK;

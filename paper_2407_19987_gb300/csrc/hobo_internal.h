@@ -27,16 +27,20 @@ struct DevLayouts {
     uint16_t* fvars = nullptr;   // [F][KF]
     float* fcoef = nullptr;      // [F]
 
-    // (3) update list by flipped bit (sparse sweep): for bit i, target
-    //     records bptr[i]..bptr[i+1]; record r updates field rtgt[r] with
-    //     the entries rbeg[r]..rbeg[r+1], each a coefficient and the other
-    //     members of the monomial besides i and the target (KU slots).
-    int64_t R = 0, U = 0;
-    int32_t* bptr = nullptr;     // [N+1]
-    int32_t* rtgt = nullptr;     // [R]
-    int32_t* rbeg = nullptr;     // [R+1]
-    float* ucoef = nullptr;      // [U]
-    uint16_t* uconds = nullptr;  // [U][KU]
+    // (3) update lists by flipped bit (sparse sweep), sliced ELL: the
+    //     target records of bit i are chunks cptr[i]..cptr[i+1] of 32 records
+    //     (lane = record); chunk c has header chdr[c] = (entry offset,
+    //     K * 64 + records), per-lane target ltgt[32c + l] and entry count
+    //     lcnt[32c + l]; entry k of lane l sits at offset + 32k + l and holds
+    //     a coefficient of a monomial containing i and the target, and the
+    //     monomial's other members (KU slots, sentinel N), zero-padded to K.
+    int64_t R = 0, U = 0, C = 0, Epad = 0;
+    int32_t* cptr = nullptr;     // [N+1]
+    int2* chdr = nullptr;        // [C]
+    uint16_t* ltgt = nullptr;    // [C][32]
+    uint16_t* lcnt = nullptr;    // [C][32]
+    float* ucoef = nullptr;      // [Epad]
+    uint16_t* uconds = nullptr;  // [Epad][KU]
 
     // (4) dense order<=3 layout: linear a[N], symmetric pair matrix S2[N][N]
     //     and symmetric cubic tensor S3[N][N][N] (zero where indices repeat),

@@ -428,20 +428,27 @@ __global__ void sweep_plain_kernel(const SweepDev p)
                     g[j] = __fadd_rn(g[j], __fmul_rn(delta, __fadd_rn(p.S2[(int64_t)i * P + j], acc)));
                 }
             } else {
-                nbytes += (int64_t)(p.bptr[i + 1] - p.bptr[i]) * 12 +
-                          (int64_t)(p.rbeg[p.bptr[i + 1]] - p.rbeg[p.bptr[i]]) * (4 + 2 * KU);
-                for (int rr = p.bptr[i]; rr < p.bptr[i + 1]; ++rr) {
-                    float acc = 0.0f;
-                    for (int e = p.rbeg[rr]; e < p.rbeg[rr + 1]; ++e) {
-                        bool on = true;
-                        for (int q = 0; q < KU; ++q) {
-                            const int v = p.uconds[(int64_t)e * KU + q];
-                            if (v < N && !bit_of(x, v)) on = false;
+                // same sums, in the same order, as the tuned kernel
+                for (int c = p.cptr[i]; c < p.cptr[i + 1]; ++c) {
+                    const int2 hd = p.chdr[c];
+                    const int nrec = hd.y & 63;
+                    nbytes += 8 + 32 * 4;
+                    for (int l = 0; l < nrec; ++l) {
+                        const int cnt = p.lcnt[32 * c + l];
+                        nbytes += (int64_t)cnt * (4 + 2 * KU);
+                        float acc = 0.0f;
+                        for (int k = 0; k < cnt; ++k) {
+                            const int64_t e = (int64_t)hd.x + 32 * k + l;
+                            bool on = true;
+                            for (int q = 0; q < KU; ++q) {
+                                const int v = p.uconds[e * KU + q];
+                                if (v < N && !bit_of(x, v)) on = false;
+                            }
+                            if (on) acc = __fadd_rn(acc, p.ucoef[e]);
                         }
-                        if (on) acc = __fadd_rn(acc, p.ucoef[e]);
+                        const int j = p.ltgt[32 * c + l];
+                        g[j] = __fadd_rn(g[j], __fmul_rn(delta, acc));
                     }
-                    const int j = p.rtgt[rr];
-                    g[j] = __fadd_rn(g[j], __fmul_rn(delta, acc));
                 }
             }
             if (E < Eb) {
@@ -466,7 +473,7 @@ SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
     p.accepts = a.accepts;
     p.coef_bytes = a.coef_bytes;
     p.write_g = a.write_g ? 1 : 0;
-    p.bptr = h->d.bptr; p.rtgt = h->d.rtgt; p.rbeg = h->d.rbeg; p.ucoef = h->d.ucoef;
+    p.cptr = h->d.cptr; p.chdr = h->d.chdr; p.ltgt = h->d.ltgt; p.lcnt = h->d.lcnt; p.ucoef = h->d.ucoef;
     p.uconds = h->d.uconds; p.S2 = h->d.S2; p.S3 = h->d.S3; p.S3col = h->d.S3col;
     return p;
 }

@@ -30,9 +30,10 @@ struct SweepDev {
     float* bestE;
     int64_t* accepts;
     int64_t* coef_bytes;
-    const int32_t* bptr;
-    const int32_t* rtgt;
-    const int32_t* rbeg;
+    const int32_t* cptr;
+    const int2* chdr;
+    const uint16_t* ltgt;
+    const uint16_t* lcnt;
     const float* ucoef;
     const uint16_t* uconds;
     const float* S2;     // [N][P]
@@ -164,32 +165,42 @@ __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __rest
     return bytes;
 }
 
-// Sparse update for a flip of bit i: lanes take target records; each sums
-// the coefficients of its entries whose conditions are all set.
+// Sparse update for a flip of bit i: lanes take the target records of a
+// chunk; each sums, in entry order, the coefficients of its entries whose
+// conditions are all set.  The entries of a step k of all lanes are adjacent,
+// so every load of the chunk is coalesced and independent of the others.
 template <int KU>
 __device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __restrict__ g,
                                                  const uint32_t* __restrict__ bs, int i, float delta,
                                                  int lane)
 {
-    const int r0 = p.bptr[i], r1 = p.bptr[i + 1];
-    const int64_t bytes = (int64_t)(r1 - r0) * 12 + (int64_t)(p.rbeg[r1] - p.rbeg[r0]) * (4 + 2 * KU);
-    for (int r = r0 + lane; r < r1; r += 32) {
-        const int j = p.rtgt[r];
-        const int e0 = p.rbeg[r], e1 = p.rbeg[r + 1];
+    const int c0 = p.cptr[i], c1 = p.cptr[i + 1];
+    int64_t entries = 0;
+    for (int c = c0; c < c1; ++c) {
+        const int2 hd = p.chdr[c];
+        const int K = hd.y >> 6, nrec = hd.y & 63;
+        const int j = p.ltgt[32 * c + lane];
+        const int cnt = p.lcnt[32 * c + lane];
+        entries += __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+        const float* __restrict__ cf = p.ucoef + hd.x + lane;
+        const uint16_t* __restrict__ cd = p.uconds + ((int64_t)hd.x + lane) * KU;
         float acc = 0.0f;
-        for (int e = e0; e < e1; ++e) {
-            const float c = p.ucoef[e];
-            uint32_t pr = 1u;
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+            if (k < cnt) {
+                const float cv = __ldg(cf + 32 * k);
+                uint32_t pr = 1u;
 #pragma unroll
-            for (int s = 0; s < KU; ++s) {
-                const int v = p.uconds[(int64_t)e * KU + s];
-                pr &= bs[v >> 5] >> (v & 31);
+                for (int s = 0; s < KU; ++s) {
+                    const int v = __ldg(cd + (int64_t)32 * k * KU + s);
+                    pr &= bs[v >> 5] >> (v & 31);
+                }
+                if (pr & 1u) acc = __fadd_rn(acc, cv);
             }
-            if (pr & 1u) acc = __fadd_rn(acc, c);
         }
-        g[j] = __fadd_rn(g[j], __fmul_rn(delta, acc));
+        if (lane < nrec) g[j] = __fadd_rn(g[j], __fmul_rn(delta, acc));
     }
-    return bytes;
+    return (int64_t)(c1 - c0) * (8 + 32 * 4) + entries * (4 + 2 * KU);
 }
 
 // Shared-memory floats one warp needs for a state of N variables: fields,
@@ -355,6 +366,201 @@ inline cudaError_t run_batch(const SweepDev* descs, const int2* items, int nitem
     kern<<<ctas, warps * 32, sm, st>>>(descs, items, nitems, counter, rf);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Learned-proposal sweep.  In a learned sweep each state scores its bits
+// with the network's per-sweep score table (a function of the scaled field
+// and the bit), orders them by descending score (ties by index) and attempts
+// the first ceil(top_frac * N) of them, 32 at a time, with the same
+// Metropolis test and random words as the plain sweep; every plain_every-th
+// sweep is a plain sweep over all bits in index order (with plain_every <= 1
+// every sweep is plain and the trajectories equal the tuned kernel's).
+// Optionally records, for states b < rec_states and sweeps s with
+// s % rec_every == 0, the features of every attempted bit at its decision:
+// (clamp(beta*g, +-vmax)/8, 2x-1, -ln(beta)/4) and the bit itself.
+// ---------------------------------------------------------------------------
+struct LearnedDev {
+    const float* tables;   // [sweeps][2][G] logits, or null when every sweep is plain
+    int G;
+    float vmax;
+    int plain_every;
+    float top_frac;
+    int rec_every, rec_states;
+    float* rec_F;          // [n_rec_sweeps][rec_states][N][3]
+    uint8_t* rec_x;        // [n_rec_sweeps][rec_states][N]
+};
+
+__host__ __device__ constexpr int learned_region_floats(int N, int WMAX)
+{
+    return 2 * ((N + 3) & ~3) + 4 * (WMAX + 1) + 8 + ((N + 3) & ~3) + (((N + 3) & ~3) / 2 + 4);
+}
+
+template <int WMAX, bool DENSE, int KU>
+__device__ __forceinline__ void anneal_state_learned(const SweepDev& p, const LearnedDev& L, int b, float* g,
+                                                     int lane)
+{
+    const int N = p.N, W = p.W;
+    const int NPAD = (N + 3) & ~3;
+    uint32_t* bs = reinterpret_cast<uint32_t*>(g + NPAD);
+    uint32_t* bxs = bs + (WMAX + 1);
+    uint32_t* rows = bs + 4 * (WMAX + 1);
+    float* score = reinterpret_cast<float*>(rows + NPAD + 8);
+    uint16_t* order = reinterpret_cast<uint16_t*>(score + NPAD);
+
+    for (int j = lane; j < N; j += 32) g[j] = p.g[(int64_t)b * N + j];
+    uint32_t x[WMAX];
+#pragma unroll
+    for (int k = 0; k < WMAX; ++k) {
+        uint32_t v = (k < W) ? p.X[(int64_t)b * W + k] : 0u;
+        const int rem = N - 32 * k;
+        if (rem <= 0) v = 0u; else if (rem < 32) v &= (1u << rem) - 1u;
+        x[k] = v;
+    }
+    float E = p.E[b], Eb = E;
+    for (int k = lane; k < W; k += 32) bxs[k] = p.resume ? p.bestX[(int64_t)b * W + k] : sel_word(x, k);
+    if (p.resume) Eb = p.bestE[b];
+    const int wsent = N >> 5;
+    const uint32_t sent = 1u << (N & 31);
+    if (!DENSE) {
+        for (int k = lane; k <= W; k += 32) {
+            uint32_t v = (k < W) ? sel_word(x, k) : 0u;
+            if (k == wsent) v |= sent;
+            bs[k] = v;
+        }
+    }
+    __syncwarp();
+
+    long long nacc = 0;
+    int64_t nbytes = 0;
+    for (int s = 0; s < p.sweeps; ++s) {
+        const float beta = __ldg(p.beta + s);
+        const uint32_t sw = (uint32_t)(p.sweep0 + s);
+        const bool plain = L.tables == nullptr || L.plain_every <= 1 ||
+                           (int)(sw % (uint32_t)L.plain_every) == L.plain_every - 1;
+        const bool rec = L.rec_F && b < L.rec_states && (s % L.rec_every) == 0;
+        const int64_t rbase = rec ? ((int64_t)(s / L.rec_every) * L.rec_states + b) * N : 0;
+        int nvisit = N;
+        if (!plain) {
+            const float* tab = L.tables + (size_t)s * 2 * L.G;
+            const float scale = (float)(L.G - 1) / (2.f * L.vmax);
+            for (int i = lane; i < N; i += 32) {
+                const float v = fminf(fmaxf(beta * g[i], -L.vmax), L.vmax);
+                const int xi = (sel_word(x, i >> 5) >> (i & 31)) & 1u;
+                const float pos = (v + L.vmax) * scale;
+                const int k = min((int)pos, L.G - 2);
+                const float fr = pos - (float)k;
+                const float* t = tab + xi * L.G;
+                score[i] = fmaf(fr, t[k + 1] - t[k], t[k]);
+            }
+            __syncwarp();
+            for (int i = lane; i < N; i += 32) {
+                const float si = score[i];
+                int rank = 0;
+                for (int j = 0; j < N; ++j) {
+                    const float sj = score[j];
+                    rank += (sj > si || (sj == si && j < i)) ? 1 : 0;
+                }
+                order[rank] = (uint16_t)i;
+            }
+            __syncwarp();
+            nvisit = max(1, min(N, (int)ceilf(L.top_frac * (float)N)));
+        }
+        for (int k0 = 0; k0 < nvisit; k0 += 32) {
+            const int kk = k0 + lane;
+            const bool valid = kk < nvisit;
+            const int i = valid ? (plain ? kk : (int)order[kk]) : 0;
+            const u32x4 r4 = philox10((uint32_t)(i >> 2), sw, (uint32_t)b, kStreamMetropolis, p.k0, p.k1);
+            const uint32_t rw = pick4(r4, i & 3);
+            int t0 = 0;
+            while (true) {
+                bool acc = false;
+                float dE = 0.0f, gi = 0.0f;
+                uint32_t xi = 0u;
+                if (valid && lane >= t0) {
+                    gi = g[i];
+                    xi = (sel_word(x, i >> 5) >> (i & 31)) & 1u;
+                    dE = xi ? -gi : gi;
+                    acc = metropolis(dE, beta, rw);
+                }
+                const uint32_t m = __ballot_sync(0xffffffffu, acc);
+                const int f = m ? __ffs(m) - 1 : 32;
+                if (rec && valid && lane >= t0 && lane <= f) {
+                    const float v = fminf(fmaxf(beta * gi, -L.vmax), L.vmax);
+                    L.rec_F[(rbase + i) * 3] = v / 8.f;
+                    L.rec_F[(rbase + i) * 3 + 1] = xi ? 1.f : -1.f;
+                    L.rec_F[(rbase + i) * 3 + 2] = -logf(fmaxf(beta, 1e-30f)) / 4.f;
+                    L.rec_x[rbase + i] = (uint8_t)xi;
+                }
+                if (m == 0u) break;
+                const int fi = __shfl_sync(0xffffffffu, i, f);
+                const float dEf = __shfl_sync(0xffffffffu, dE, f);
+                const int fw = fi >> 5;
+                const uint32_t fm = 1u << (fi & 31);
+                const float delta = (sel_word(x, fw) & fm) ? -1.0f : 1.0f;
+#pragma unroll
+                for (int k = 0; k < WMAX; ++k) x[k] ^= (k == fw) ? fm : 0u;
+                E = __fadd_rn(E, dEf);
+                ++nacc;
+                if (E < Eb) {
+                    Eb = E;
+                    for (int k = lane; k < W; k += 32) bxs[k] = sel_word(x, k);
+                }
+                if (DENSE) {
+                    nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1)>(p, g, x, fi, delta, lane, rows);
+                } else {
+                    if (lane == 0) bs[fw] = sel_word(x, fw) | (fw == wsent ? sent : 0u);
+                    __syncwarp();
+                    nbytes += sparse_update<KU>(p, g, bs, fi, delta, lane);
+                }
+                __syncwarp();
+                t0 = f + 1;
+                if (t0 >= 32) break;
+            }
+        }
+    }
+
+    for (int k = lane; k < W; k += 32) {
+        p.X[(int64_t)b * W + k] = sel_word(x, k);
+        p.bestX[(int64_t)b * W + k] = bxs[k];
+    }
+    if (p.write_g)
+        for (int j = lane; j < N; j += 32) p.g[(int64_t)b * N + j] = g[j];
+    if (lane == 0) {
+        p.E[b] = E;
+        p.bestE[b] = Eb;
+        if (p.accepts) p.accepts[b] += nacc;
+        if (p.coef_bytes) p.coef_bytes[b] += nbytes;
+    }
+}
+
+template <int WMAX, bool DENSE, int KU>
+__global__ void __launch_bounds__(kSweepWarps * 32, 4)
+sweep_learned_kernel(const SweepDev p, const LearnedDev L)
+{
+    extern __shared__ float sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x * kSweepWarps + warp;
+    if (b >= p.B) return;
+    anneal_state_learned<WMAX, DENSE, KU>(p, L, b, sm + (size_t)warp * learned_region_floats(p.N, WMAX), lane);
+}
+
+template <int WMAX, bool DENSE, int KU>
+inline cudaError_t run_learned(const SweepDev& p, const LearnedDev& L, cudaStream_t st)
+{
+    const size_t sm = sizeof(float) * (size_t)learned_region_floats(p.N, WMAX) * kSweepWarps;
+    auto kern = sweep_learned_kernel<WMAX, DENSE, KU>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)((p.B + kSweepWarps - 1) / kSweepWarps), kSweepWarps * 32, sm, st>>>(p, L);
+    return cudaGetLastError();
+}
+
+template <bool DENSE, int KU>
+cudaError_t dispatch_learned(const SweepDev& p, const LearnedDev& L, cudaStream_t st);
+template <> cudaError_t dispatch_learned<true, 1>(const SweepDev&, const LearnedDev&, cudaStream_t);
+template <> cudaError_t dispatch_learned<false, 1>(const SweepDev&, const LearnedDev&, cudaStream_t);
+template <> cudaError_t dispatch_learned<false, 2>(const SweepDev&, const LearnedDev&, cudaStream_t);
+template <> cudaError_t dispatch_learned<false, 6>(const SweepDev&, const LearnedDev&, cudaStream_t);
 
 template <int WMAX, bool DENSE, int KU>
 inline cudaError_t run_tuned(const SweepDev& p, cudaStream_t st)

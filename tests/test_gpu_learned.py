@@ -1,0 +1,223 @@
+"""GPU parity of the learned proposal: the network's forward and backward
+passes against the oracle's float64 network on the same bf16-rounded
+weights, the optimiser's first step against its closed form, and the
+learned sweep (hobo_anneal_learned) against the oracle's learned annealer
+on integer instances, trajectory for trajectory."""
+import math
+
+import numpy as np
+import pytest
+
+import gpuh
+import workloads as W
+from oracle import oracle as O
+from test_oracle_mlp import identity_net
+
+pytestmark = pytest.mark.gpu
+
+
+def _H():
+    import paper_2407_19987_gb300 as H
+    return H
+
+
+def _flat(w, H):
+    return np.concatenate([w["W1"].reshape(-1), w["b1"], w["W2"].reshape(-1), w["b2"], w["w3"],
+                           np.asarray(w["b3"]).reshape(-1)]).astype(np.float32)
+
+
+def _features(rng, n):
+    F = np.empty((n, 3), np.float32)
+    F[:, 0] = np.clip(rng.standard_normal(n) * 2.0, -4, 4)
+    F[:, 1] = rng.integers(0, 2, n) * 2 - 1
+    F[:, 2] = rng.uniform(-1.0, 0.6, n)
+    return F
+
+
+def _abs_net(w):
+    return {k: np.abs(v) for k, v in w.items()}
+
+
+def test_mlp_forward_matches_oracle():
+    T = gpuh.torch()
+    m = _H().MLP(hidden=256, seed=3)
+    w = m.unpack(m.params(rounded=True))
+    rng = np.random.default_rng(1)
+    F = _features(rng, 1000)   # 15 full 64-row tiles and a ragged one
+    got = m.forward(T.from_numpy(F).cuda()).cpu().numpy().astype(np.float64)
+    ref = O.mlp_forward(w, F)
+    # float32 sums of at most H+1 products per unit in two layers: bound the
+    # error by 2^-15.6 (2e-5) of the same network run on magnitudes
+    scale = O.mlp_forward(_abs_net(w), np.abs(F))
+    assert np.all(np.abs(got - ref) <= 2e-5 * scale)
+    assert m.forward(T.zeros((0, 3), device="cuda")).numel() == 0
+    m.close()
+
+
+def test_mlp_loss_and_gradients_match_oracle():
+    T = gpuh.torch()
+    m = _H().MLP(hidden=64, seed=4)
+    w = m.unpack(m.params(rounded=True))
+    rng = np.random.default_rng(2)
+    n = 777
+    F = _features(rng, n)
+    y = (rng.random(n) < 0.3).astype(np.float32)
+    loss, g = m.loss_grad(T.from_numpy(F).cuda(), T.from_numpy(y).cuda())
+    rl, rg = O.mlp_loss_grad(w, F, y)
+    assert abs(float(loss.item()) - rl) <= 1e-5 * abs(rl)
+    got = m.unpack(g.cpu().numpy())
+    for k in ("W1", "b1", "W2", "b2", "w3", "b3"):
+        ref = rg[k].reshape(got[k].shape)
+        tol = 2e-4 * np.max(np.abs(ref)) + 1e-7
+        assert np.max(np.abs(got[k] - ref)) <= tol, k
+    m.close()
+
+
+def test_adam_first_step_moves_each_weight_by_lr():
+    # from zero moments, Adam's first update is lr * g / (|g| + eps)
+    T = gpuh.torch()
+    m = _H().MLP(hidden=32, seed=5)
+    rng = np.random.default_rng(3)
+    F = T.from_numpy(_features(rng, 300)).cuda()
+    y = T.from_numpy((rng.random(300) < 0.5).astype(np.float32)).cuda()
+    w0 = m.params(rounded=False)
+    _, g = m.loss_grad(F, y)
+    g = g.cpu().numpy()
+    lr = 1e-3
+    m.train_step(F, y, lr)
+    T.cuda.synchronize()
+    w1 = m.params(rounded=False)
+    big = np.abs(g) > 1e-5
+    step = (w0 - w1)[big]
+    np.testing.assert_allclose(step, lr * np.sign(g[big]), rtol=1e-4, atol=1e-6 * np.max(np.abs(w0)))
+    assert np.array_equal(w1[g == 0], w0[g == 0])
+    # rounded copies follow the masters
+    r = m.params(rounded=True)
+    assert np.array_equal(r, T.from_numpy(w1).bfloat16().float().numpy())
+    m.close()
+
+
+def test_training_reduces_loss():
+    T = gpuh.torch()
+    m = _H().MLP(hidden=128, seed=6)
+    rng = np.random.default_rng(4)
+    Fn = _features(rng, 4096)
+    yn = ((Fn[:, 0] * Fn[:, 1]) < 0).astype(np.float32)
+    F, y = T.from_numpy(Fn).cuda(), T.from_numpy(yn).cuda()
+    loss = T.zeros(1, device="cuda")
+    l0, _ = m.loss_grad(F, y)
+    l0 = float(l0.item())
+    for _ in range(200):
+        m.train_step(F, y, 3e-3, loss)
+    l1, _ = m.loss_grad(F, y)
+    assert float(l1.item()) < 0.5 * l0
+
+
+def test_save_load_roundtrip(tmp_path):
+    T = gpuh.torch()
+    m = _H().MLP(hidden=96, seed=7)
+    p = str(tmp_path / "net.bin")
+    m.save(p)
+    m2 = _H().MLP.load(p)
+    assert m2.hidden == 96
+    assert np.array_equal(m.params(rounded=True), m2.params(rounded=True))
+    F = T.from_numpy(_features(np.random.default_rng(5), 130)).cuda()
+    assert T.equal(m.forward(F), m2.forward(F))
+    with open(p, "r+b") as f:
+        f.write(b"{\"format\": \"other\"}\n")
+    with pytest.raises(_H().HoboError):
+        _H().MLP.load(p)
+
+
+def _set_net(w, H=32):
+    m = _H().MLP(hidden=H, seed=0)
+    m.set_params(_flat(w, H))
+    return m
+
+
+def _compare(r, ref, N):
+    np.testing.assert_array_equal(gpuh.to_host_bits(r["bestX"], N), ref["bestX"])
+    np.testing.assert_array_equal(r["bestE"].cpu().numpy(), ref["bestE"])
+    np.testing.assert_array_equal(gpuh.to_host_bits(r["X"], N), ref["X"])
+    np.testing.assert_array_equal(r["E"].cpu().numpy().astype(np.float64), ref["E"])
+    np.testing.assert_array_equal(r["accepts"].cpu().numpy(), ref["accepts"])
+
+
+CASES = [
+    ("tiny_dense", lambda: W.tiny_dense(1), 0, 40, (5.0, 0.05, 60)),
+    ("dense_int_N64", lambda: W.random_sparse(40, 64, 3, 0.5, "int"), 4, 24, (30.0, 0.1, 12)),
+    ("order3_N45", lambda: W.random_sparse(42, 45, 3, 0.05, "int"), 0, 40, (10.0, 0.1, 20)),
+    ("order4_N96", lambda: W.sparse_order4(5003), 0, 24, (8.0, 0.05, 16)),
+    ("order6_N20", lambda: W.random_sparse(45, 20, 6, 0.02, "int"), 0, 20, (10.0, 0.1, 15)),
+]
+
+
+@pytest.mark.parametrize("name,maker,flags,B,sched", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("plain_every,top_frac", [(3, 1.0), (4, 0.6), (2, 0.1)])
+def test_learned_anneal_matches_oracle(name, maker, flags, B, sched, plain_every, top_frac):
+    inst = maker()
+    betas = W.geometric_betas(*sched)
+    h = gpuh.make(inst, flags)
+    w = identity_net()
+    m = _set_net(w)
+    r = _H().anneal_learned(h, m, 77, B, betas, plain_every=plain_every, top_frac=top_frac,
+                            want_final=True, want_accepts=True)
+    ref = O.anneal_learned(inst, 77, B, betas, w, plain_every=plain_every, top_frac=top_frac)
+    _compare(r, ref, inst.N)
+    h.close()
+
+
+@pytest.mark.parametrize("net", ["none", "constant", "plain_every_1"])
+def test_learned_anneal_reduces_to_tuned_anneal(net):
+    inst = W.random_sparse(46, 70, 3, 0.1, "normal")
+    betas = W.geometric_betas(5.0, 0.05, 30)
+    h = gpuh.make(inst)
+    m, pe = None, 4
+    if net == "constant":
+        w = identity_net()
+        w = {k: np.zeros_like(v) for k, v in w.items()}
+        w["b3"] = np.array([0.25])
+        m = _set_net(w)
+    elif net == "plain_every_1":
+        m, pe = _H().MLP(hidden=64, seed=8), 1
+    r = _H().anneal_learned(h, m, 5, 50, betas, plain_every=pe, want_final=True, want_accepts=True)
+    t = h.anneal(5, 50, betas, mode=0, want_final=True, want_accepts=True)
+    for k in ("bestX", "bestE", "X", "E", "accepts"):
+        assert gpuh.torch().equal(r[k], t[k]), k
+    h.close()
+
+
+def test_recorded_features_and_labels_match_oracle():
+    inst = W.sparse_order4(5004, N=64, density=0.03)
+    betas = W.geometric_betas(8.0, 0.05, 24)
+    h = gpuh.make(inst)
+    w = identity_net()
+    m = _set_net(w)
+    for net in (None, m):
+        r = _H().anneal_learned(h, net, 31, 40, betas, plain_every=3, top_frac=0.5, rec_every=5, rec_states=7)
+        ref = O.anneal_learned(inst, 31, 40, betas, w if net is not None else None, plain_every=3,
+                               top_frac=0.5, rec_every=5, rec_B=7)
+        F = r["rec_F"].cpu().numpy()
+        np.testing.assert_array_equal(r["rec_y"].cpu().numpy(), ref["rec_y"])
+        np.testing.assert_array_equal(F[:, :2], ref["rec_F"][:, :2])
+        np.testing.assert_allclose(F[:, 2], ref["rec_F"][:, 2], rtol=2.5e-7, atol=0)
+        if net is None:
+            assert np.all(ref["rec_y"] >= 0)
+        else:
+            assert np.any(ref["rec_y"] < 0)
+    h.close()
+
+
+def test_learned_anneal_arguments():
+    inst = W.random_sparse(47, 300, 3, 0.01, "normal")
+    h = gpuh.make(inst)
+    with pytest.raises(_H().HoboError):
+        _H().anneal_learned(h, None, 1, 8, W.geometric_betas(5, .1, 4))   # N > 256
+    h.close()
+    h = gpuh.make(W.tiny_dense(1))
+    r = _H().anneal_learned(h, None, 1, 0, W.geometric_betas(5, .1, 4))
+    assert r["bestE"].numel() == 0
+    r = _H().anneal_learned(h, None, 1, 16, np.zeros(0, np.float32), want_final=True)
+    X0 = O.init_states(1, 12, 16)
+    np.testing.assert_array_equal(gpuh.to_host_bits(r["bestX"], 12), X0)
+    h.close()
