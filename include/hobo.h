@@ -322,18 +322,27 @@ int hobo_mlp_train_step(hobo_mlp_h m, const float* F, const float* y, int64_t n,
 int hobo_mlp_save(hobo_mlp_h m, const char* path);
 int hobo_mlp_load(hobo_mlp_h* out, const char* path);
 
+#define HOBO_SELECT_ORDER      0
+#define HOBO_SELECT_THRESHOLD  1
+
 typedef struct {
     int plain_every;     /* every plain_every-th sweep is plain (default 4);
                             <= 1: all sweeps plain (network unused) */
-    float top_frac;      /* learned sweeps attempt the top ceil(top_frac*N)
-                            bits by score (0 = 1.0: all bits) */
+    int select;          /* HOBO_SELECT_ORDER (0): learned sweeps attempt the
+                            top ceil(top_frac*N) bits in descending score
+                            (ties by index); HOBO_SELECT_THRESHOLD (1): they
+                            attempt, in index order, the bits whose score
+                            (logit) is >= threshold */
+    float top_frac;      /* order mode: fraction of bits attempted (0 = 1.0) */
+    float threshold;     /* threshold mode: logit threshold */
     int table_size;      /* grid points of the per-sweep score table (0 = 1024) */
     float vmax;          /* clamp of beta*g in the features (0 = 32) */
     int rec_every;       /* record sweeps s with s % rec_every == 0 (0: none) */
     int rec_states;      /* ... for states b < rec_states */
     float* rec_F;        /* device [ceil(sweeps/rec_every)][rec_states][N][3]: features */
     float* rec_y;        /* device [..][rec_states][N]: label 1 if the bit then
-                            differs from the state's final best state, else 0 */
+                            differs from the state's final best state, 0 if
+                            not, -1 if the bit was not attempted */
     uint32_t* X_out;     /* device [B][W] or NULL: final states */
     float* E_out;        /* device [B] or NULL: final float32 energies */
     int64_t* accepts;    /* device [B] or NULL: accepted flips (added to) */
@@ -343,10 +352,12 @@ typedef struct {
 
 /*
  * hobo_anneal_learned -- hobo_anneal with the learned proposal: in learned
- * sweeps each state attempts its bits in descending network score (ties by
- * index), the top ceil(top_frac*N) of them, with the unchanged Metropolis
- * test and random words; every plain_every-th sweep is the plain sweep
- * over all bits in order, which stays the fallback.  Scores come from a
+ * sweeps each state scores its bits at the start of the sweep and attempts
+ * either the top ceil(top_frac*N) of them in descending score (ties by
+ * index) or those scoring >= threshold in index order (opts->select), with
+ * the unchanged Metropolis test and random words; every plain_every-th
+ * sweep is the plain sweep over all bits in order, which stays the
+ * fallback.  Scores come from a
  * per-sweep table of the network over (clamped beta*g, bit), evaluated by
  * the library's forward kernel and read with linear interpolation.  m may
  * be NULL (all sweeps plain).  Requires N <= 256.  Same seed, beta, outputs

@@ -480,11 +480,12 @@ double orc_mlp_loss_grad(int H, const double* W1, const double* b1, const double
 /* scored by the network on its features                                 */
 /*   f0 = clamp(beta_s * g_i, -vmax, vmax) / 8                           */
 /*   f1 = 2 x_i - 1,  f2 = -ln(beta_s) / 4                               */
-/* (f0 in float32 from the float32 field, f1 exact, f2 in float64), the  */
-/* bits are ordered by descending score with ties broken by ascending    */
-/* index, and the first max(1, ceil(top_frac * N)) of them are attempted */
-/* in that order with the same Metropolis test and random word (bit i,  */
-/* sweep s) as a plain sweep.                                            */
+/* (f0 in float32 from the float32 field, f1 exact, f2 in float64).      */
+/* select 0: the bits are ordered by descending score with ties broken   */
+/* by ascending index, and the first max(1, ceil(top_frac * N)) of them  */
+/* are attempted in that order; select 1: the bits with score >=         */
+/* threshold are attempted in index order.  Each attempt uses the same   */
+/* Metropolis test and random word (bit i, sweep s) as a plain sweep.    */
 /* Recording: for states b < rec_B and sweeps with s % rec_every == 0,   */
 /* row (s / rec_every, b, i) gets the features of bit i at its decision  */
 /* and its bit then (rec_x); rows of bits not attempted are left alone.  */
@@ -506,7 +507,8 @@ static float clampf_(float v, float lo, float hi) { return v < lo ? lo : (v > hi
 void orc_anneal_learned(const int32_t* idx, const double* coef, int64_t nnz, int order, int N,
                         uint64_t seed, int64_t B, const float* betas, int sweeps,
                         int H, const double* W1, const double* b1, const double* W2, const double* b2,
-                        const double* w3, double b3, int plain_every, float top_frac, float vmax,
+                        const double* w3, double b3, int plain_every, int select, float top_frac,
+                        double threshold, float vmax,
                         uint8_t* Xfinal, double* Efinal, uint8_t* Xbest, double* Ebest, int64_t* accepts,
                         int rec_every, int64_t rec_B, float* rec_F, uint8_t* rec_x)
 {
@@ -539,12 +541,18 @@ void orc_anneal_learned(const int32_t* idx, const double* coef, int64_t nnz, int
                     F[i * 3 + 2] = f2;
                 }
                 orc_mlp_forward(H, W1, b1, W2, b2, w3, b3, F, N, sc);
-                for (int i = 0; i < N; ++i) { ord[i].score = sc[i]; ord[i].i = i; }
-                qsort(ord, (size_t)N, sizeof(scored_t), by_score_desc);
-                float want = top_frac * (float)N;
-                nvisit = (int)ceilf(want);
-                if (nvisit > N) nvisit = N;
-                if (nvisit < 1) nvisit = 1;
+                if (select == 0) {
+                    for (int i = 0; i < N; ++i) { ord[i].score = sc[i]; ord[i].i = i; }
+                    qsort(ord, (size_t)N, sizeof(scored_t), by_score_desc);
+                    float want = top_frac * (float)N;
+                    nvisit = (int)ceilf(want);
+                    if (nvisit > N) nvisit = N;
+                    if (nvisit < 1) nvisit = 1;
+                } else {
+                    nvisit = 0;
+                    for (int i = 0; i < N; ++i)
+                        if (sc[i] >= threshold) ord[nvisit++].i = i;
+                }
             }
             const int rec = rec_F && b < rec_B && (s % rec_every) == 0;
             const int64_t rbase = rec ? ((int64_t)(s / rec_every) * rec_B + b) * N : 0;

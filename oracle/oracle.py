@@ -56,7 +56,7 @@ def lib():
         _lib.orc_anneal_naive.argtypes = [P, P, i64, i32, i32, u64, i64, i64, P, i32,
                                           P, P, P, P, P]
         _lib.orc_anneal_learned.argtypes = [P, P, i64, i32, i32, u64, i64, P, i32,
-                                            i32, P, P, P, P, P, dbl, i32, flt, flt,
+                                            i32, P, P, P, P, P, dbl, i32, i32, flt, dbl, flt,
                                             P, P, P, P, P, i32, i64, P, P]
         _lib.orc_mlp_forward.argtypes = [i32, P, P, P, P, P, dbl, P, i64, P]
         _lib.orc_mlp_loss_grad.restype = dbl
@@ -196,7 +196,8 @@ def mlp_loss_grad(w: dict, F: np.ndarray, y: np.ndarray):
 
 
 def anneal_learned(inst, seed: int, B: int, betas: np.ndarray, w: dict | None, plain_every: int = 4,
-                   top_frac: float = 1.0, vmax: float = 32.0, rec_every: int = 0, rec_B: int = 0) -> dict:
+                   top_frac: float = 1.0, vmax: float = 32.0, rec_every: int = 0, rec_B: int = 0,
+                   select: int = 0, threshold: float = 0.0) -> dict:
     """Oracle annealer with the learned proposal (network weights ``w`` as
     in mlp_forward, or None for plain sweeps only).  With recording, returns
     rec_F [rows, 3], rec_x (0xFF where a bit was not attempted) and the
@@ -222,7 +223,7 @@ def anneal_learned(inst, seed: int, B: int, betas: np.ndarray, w: dict | None, p
     recF = np.zeros((max(nrows, 1), 3), np.float32)
     recx = np.full(max(nrows, 1), 0xFF, np.uint8)
     lib().orc_anneal_learned(_p(idx), _p(coef), idx.shape[0], inst.order, N, seed, B, _p(betas), S,
-                             H, *wp, b3, plain_every, float(top_frac), float(vmax),
+                             H, *wp, b3, plain_every, int(select), float(top_frac), float(threshold), float(vmax),
                              _p(Xf), _p(Ef), _p(Xb), _p(Eb), _p(acc),
                              max(rec_every, 1), rB, _p(recF) if rec else None, _p(recx) if rec else None)
     out = dict(X=Xf, E=Ef, bestX=Xb, bestE=Eb, accepts=acc)

@@ -63,7 +63,8 @@ class hobo_batch_opts(C.Structure):
 
 
 class hobo_learned_opts(C.Structure):
-    _fields_ = [("plain_every", C.c_int), ("top_frac", C.c_float), ("table_size", C.c_int),
+    _fields_ = [("plain_every", C.c_int), ("select", C.c_int), ("top_frac", C.c_float), ("threshold", C.c_float),
+                ("table_size", C.c_int),
                 ("vmax", C.c_float), ("rec_every", C.c_int), ("rec_states", C.c_int),
                 ("rec_F", C.c_void_p), ("rec_y", C.c_void_p), ("X_out", C.c_void_p), ("E_out", C.c_void_p),
                 ("accepts", C.c_void_p), ("ev_begin", C.c_void_p), ("ev_end", C.c_void_p)]
@@ -451,8 +452,12 @@ class MLP:
         _check(load_library().hobo_mlp_save(self._h, path.encode()))
 
 
+SELECT_ORDER, SELECT_THRESHOLD = 0, 1
+
+
 def anneal_learned(inst: Instance, mlp, seed: int, B: int, betas: np.ndarray, *, plain_every: int = 4,
-                   top_frac: float = 1.0, table_size: int = 0, vmax: float = 0.0, rec_every: int = 0,
+                   select: int = SELECT_ORDER, top_frac: float = 1.0, threshold: float = 0.0,
+                   table_size: int = 0, vmax: float = 0.0, rec_every: int = 0,
                    rec_states: int = 0, want_final: bool = False, want_accepts: bool = False, events=None,
                    stream=None) -> dict:
     """hobo_anneal_learned through the C ABI; returns CUDA tensors."""
@@ -471,7 +476,8 @@ def anneal_learned(inst: Instance, mlp, seed: int, B: int, betas: np.ndarray, *,
         recF = torch.zeros((nr, 3), dtype=torch.float32, device=dev)
         recy = torch.zeros(nr, dtype=torch.float32, device=dev)
     ev0, ev1 = (None, None) if events is None else (_event_handle(events[0]), _event_handle(events[1]))
-    o = hobo_learned_opts(plain_every, top_frac, table_size, vmax, rec_every, rec_states, _ptr(recF), _ptr(recy),
+    o = hobo_learned_opts(plain_every, select, top_frac, threshold, table_size, vmax, rec_every, rec_states,
+                          _ptr(recF), _ptr(recy),
                           _ptr(X), _ptr(E), _ptr(acc), ev0, ev1)
     _check(load_library().hobo_anneal_learned(inst.handle, None if mlp is None else mlp.handle,
                                               C.c_uint64(seed & (2 ** 64 - 1)), B,

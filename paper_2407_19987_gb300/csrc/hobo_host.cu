@@ -92,7 +92,7 @@ static int upload(T** dst, const std::vector<T>& src)
 
 static void free_layouts(DevLayouts& d)
 {
-    void* ptrs[] = {d.tvars, d.tcoef32, d.tcoef64, d.tfix, d.fptr, d.fvars, d.fcoef, d.cptr, d.chdr,
+    void* ptrs[] = {d.tvars, d.tfix, d.fptr, d.fvars, d.ffix, d.cptr, d.chdr,
                     d.ltgt, d.lcnt, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf,
                     d.C3fix, d.S2fix, d.afix, d.pair_m, d.pair_j};
     for (void* p : ptrs)
@@ -161,9 +161,7 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
     {
         const int KS = h->KS;
         std::vector<uint16_t> tv((size_t)std::max<int64_t>(M, 1) * KS, (uint16_t)N);
-        std::vector<float> c32((size_t)M);
-        std::vector<double> c64((size_t)M);
-        std::vector<long long> cfix((size_t)M);
+        std::vector<long long> cfix((size_t)std::max<int64_t>(M, 1), 0);
         // fixed-point scale: sum |c| * 2^S < 2^62 keeps every partial sum in range
         int S = 0;
         if (abs_sum > 0.0) {
@@ -174,37 +172,36 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
         d.fix_shift = S;
         for (int64_t t = 0; t < M; ++t) {
             for (int q = 0; q < mono[t].m.d; ++q) tv[(size_t)t * KS + q] = mono[t].m.v[q];
-            c32[t] = (float)mono[t].c;
-            c64[t] = mono[t].c;
             cfix[t] = std::llrint(std::ldexp(mono[t].c, S));
         }
         int rc;
-        if ((rc = upload(&d.tvars, tv)) || (rc = upload(&d.tcoef32, c32)) || (rc = upload(&d.tcoef64, c64)) ||
-            (rc = upload(&d.tfix, cfix)))
+        if ((rc = upload(&d.tvars, tv)) || (rc = upload(&d.tfix, cfix)))
             return rc;
     }
     // (2) field list by variable
     {
-        const int KF = h->KF;
+        const int KF = K - 1;
+        const int KV = KF <= 2 ? 2 : (KF <= 4 ? 4 : 8);
+        d.KV = KV;
         std::vector<int64_t> ptr((size_t)N + 1, 0);
         for (auto& e : mono)
             for (int q = 0; q < e.m.d; ++q) ptr[e.m.v[q] + 1]++;
         for (int j = 0; j < N; ++j) ptr[j + 1] += ptr[j];
         d.F = ptr[N];
         std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
-        std::vector<uint16_t> fv((size_t)std::max<int64_t>(d.F, 1) * KF, (uint16_t)N);
-        std::vector<float> fc((size_t)std::max<int64_t>(d.F, 1), 0.0f);
+        std::vector<uint16_t> fv((size_t)std::max<int64_t>(d.F, 1) * KV, (uint16_t)N);
+        std::vector<long long> fc((size_t)std::max<int64_t>(d.F, 1), 0);
         for (auto& e : mono)
             for (int q = 0; q < e.m.d; ++q) {
                 const int j = e.m.v[q];
                 const int64_t at = fill[j]++;
                 int s = 0;
                 for (int r = 0; r < e.m.d; ++r)
-                    if (r != q) fv[(size_t)at * KF + s++] = e.m.v[r];
-                fc[at] = (float)e.c;
+                    if (r != q) fv[(size_t)at * KV + s++] = e.m.v[r];
+                fc[at] = std::llrint(std::ldexp(e.c, d.fix_shift));
             }
         int rc;
-        if ((rc = upload(&d.fptr, ptr)) || (rc = upload(&d.fvars, fv)) || (rc = upload(&d.fcoef, fc)))
+        if ((rc = upload(&d.fptr, ptr)) || (rc = upload(&d.fvars, fv)) || (rc = upload(&d.ffix, fc)))
             return rc;
     }
 

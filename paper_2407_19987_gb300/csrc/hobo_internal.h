@@ -12,20 +12,22 @@ namespace hobo {
 struct DevLayouts {
     // (1) folded monomial list, all degrees, KS (4 or 8) variable slots per
     //     monomial padded with the sentinel index N (whose bit reads as 1).
+    //     Coefficients are fixed point: round(c * 2^fix_shift) with
+    //     fix_shift chosen so that the sum of all |c| stays below 2^62, so
+    //     every partial sum of them is exact in 64-bit integers.
     int64_t M = 0;
     uint16_t* tvars = nullptr;   // [M][KS]
-    float* tcoef32 = nullptr;    // [M]
-    double* tcoef64 = nullptr;   // [M]
-    long long* tfix = nullptr;   // [M] round(c * 2^fix_shift), exact re-score
+    long long* tfix = nullptr;   // [M]
     int fix_shift = 0;
 
-    // (2) field list by variable: entry e of variable j holds the
-    //     coefficient of a monomial containing j and its other members
-    //     (KF = max(order-1,1) slots, sentinel N).
+    // (2) field list by variable: entry e of variable j holds the fixed-
+    //     point coefficient of a monomial containing j and its other
+    //     members (KV = 2, 4 or 8 >= order-1 slots, sentinel N).
     int64_t F = 0;
+    int KV = 2;
     int64_t* fptr = nullptr;     // [N+1]
-    uint16_t* fvars = nullptr;   // [F][KF]
-    float* fcoef = nullptr;      // [F]
+    uint16_t* fvars = nullptr;   // [F][KV]
+    long long* ffix = nullptr;   // [F]
 
     // (3) update lists by flipped bit (sparse sweep), sliced ELL: the
     //     target records of bit i are chunks cptr[i]..cptr[i+1] of 32 records

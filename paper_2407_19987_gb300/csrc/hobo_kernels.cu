@@ -33,199 +33,219 @@ cudaError_t launch_init_states(uint32_t* X, int B, int N, int W, uint64_t seed, 
 }
 
 // ===========================================================================
-// Term-list contraction on CUDA cores.  A block holds 32 states (one per
-// lane) with their bits transposed in shared memory (word w of state b at
-// [w][b], plus the sentinel bit N that reads as 1).  Warps split the
-// variables: for variable j the field is the sum of the coefficients of the
-// monomials containing j whose other members are all set.  The energy is
-// the sum over monomials whose members are all set.
+// Term-list contraction on CUDA cores, in exact fixed point.
+//
+// Coefficients are the 64-bit integers round(c * 2^S) of the instance's
+// monomial and field lists, S chosen so that the sum of all |c| * 2^S stays
+// below 2^62: every partial sum is exact, so the result does not depend on
+// how the sums are split between threads and blocks, and the float32 (or
+// float64) outputs are the sums rounded once.  Integer instances (sum of
+// |c| < 2^24) come out exact.
+//
+// A block holds 32 states, one per lane.  Their bits are transposed into
+// column masks in shared memory: bit l of cm[v] is bit v of state b0 + l
+// (cm[N] = all ones is the padding sentinel), so the members of a monomial
+// are tested for all 32 states with one AND per member.  Blocks with
+// blockIdx.y < ES each sum a slice of the monomial list into the energies
+// (64-bit atomics into acc); the others take eight variables each (one per
+// warp), and warp j sums its field list: g_j = sum of the coefficients of
+// the monomials containing j whose other members are all set (Sec. II.C
+// energy differentiated in x_j; dE_j = (1 - 2 x_j) g_j).  Lists are read
+// 32 records at a time, coalesced, through a per-warp staging buffer.
 // ===========================================================================
-constexpr int kTermThreads = 256;
+constexpr int kEfThreads = 256;
+constexpr int kEfWarps = kEfThreads / 32;
 
-// Compensated summation (Kahan): acc + comp tracks the exact running sum to
-// within a few units in the last place, whatever the number of terms.
-__device__ __forceinline__ void kahan_add(float& acc, float& comp, float v)
+template <int KV> struct VarRow;
+template <> struct VarRow<2> { using T = uint32_t; };
+template <> struct VarRow<4> { using T = uint2; };
+template <> struct VarRow<8> { using T = uint4; };
+
+template <int KV>
+__device__ __forceinline__ int row_var(const typename VarRow<KV>::T& r, int s)
 {
-    const float y = __fsub_rn(v, comp);
-    const float t = __fadd_rn(acc, y);
-    comp = __fsub_rn(__fsub_rn(t, acc), y);
-    acc = t;
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(&r);
+    return (int)((w[s >> 1] >> ((s & 1) * 16)) & 0xFFFFu);
 }
 
-template <bool FLIP>
-__global__ void __launch_bounds__(kTermThreads)
-energy_terms_kernel(const uint32_t* __restrict__ X, int B, int N, int W,
-                    const int64_t* __restrict__ fptr, const uint16_t* __restrict__ fvars,
-                    const float* __restrict__ fcoef, int KF,
-                    const uint16_t* __restrict__ tvars, const float* __restrict__ tcoef,
-                    int64_t M, int K, int KS, float* __restrict__ out_g, float* __restrict__ out_E)
+struct EfArgs {
+    const uint32_t* X;
+    int B, N, W;
+    const uint16_t* tvars;
+    const long long* tfix;
+    int64_t M;
+    int64_t per_slice;   // monomials per energy block
+    int ES;              // energy blocks per 32 states
+    const int64_t* fptr;
+    const uint16_t* fvars;
+    const long long* ffix;
+    int S;               // fixed-point shift
+    int flip;            // write dE_j = (1 - 2 x_j) g_j instead of g_j
+    float* out_g;        // [B][N] or null
+    unsigned long long* acc;   // [B] energy accumulators (zeroed)
+};
+
+// Sum of the records rec0..rec1 of a list whose variables are all set, per
+// lane (state).  NV variables per record (row width KV), sentinel cm[N].
+template <int NV, int KV>
+__device__ __forceinline__ long long sum_active(const uint32_t* cm, const uint16_t* __restrict__ vars,
+                                                const long long* __restrict__ coef, int64_t rec0,
+                                                int64_t rec1, typename VarRow<KV>::T* sv, long long* sc,
+                                                int lane)
 {
-    extern __shared__ uint32_t smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    using Row = typename VarRow<KV>::T;
+    const uint32_t lbit = 1u << lane;
+    const Row* rows = reinterpret_cast<const Row*>(vars);
+    long long s = 0;
+    for (int64_t base = rec0; base < rec1; base += 32) {
+        const int64_t e = base + lane;
+        if (e < rec1) {
+            sv[lane] = __ldg(rows + e);
+            sc[lane] = __ldg(coef + e);
+        }
+        __syncwarp();
+        const int n = (int)(rec1 - base < 32 ? rec1 - base : 32);
+#pragma unroll 4
+        for (int q = 0; q < n; ++q) {
+            const Row r = sv[q];
+            uint32_t m = lbit;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) m &= cm[row_var<KV>(r, v)];
+            if (m) s += sc[q];
+        }
+        __syncwarp();
+    }
+    return s;
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kEfThreads)
+energy_fields_kernel(const EfArgs a)
+{
+    constexpr int KF = ORDER - 1;
+    constexpr int KV = KF <= 2 ? 2 : (KF <= 4 ? 4 : 8);
+    constexpr int KS = ORDER <= 4 ? 4 : 8;
+    constexpr int KR = KV > KS ? KV : KS;
+    using RowS = typename VarRow<KR>::T;
+    __shared__ uint32_t cm[HOBO_MAX_N + 1];
+    __shared__ RowS stv[kEfWarps][32];
+    __shared__ long long stc[kEfWarps][32];
+    __shared__ long long red[kEfWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int b0 = blockIdx.x * 32;
-    const int nb = min(32, B - b0);
-    const int WS = W + 1;
-    uint32_t* bits = smem;                              // [WS][32]
-    float* red = reinterpret_cast<float*>(bits + WS * 32);   // [nwarps][32]
-    float* gs = red + nwarps * 32;                      // [32][N+1]
-    const int NP = N + 1;
+    const int nb = min(32, a.B - b0);
 
-    for (int q = threadIdx.x; q < WS * 32; q += blockDim.x) {
-        const int w = q >> 5, b = q & 31;
-        uint32_t v = 0;
-        if (w < W && b < nb) {
-            v = X[(int64_t)(b0 + b) * W + w];
-            const int rem = N - 32 * w;
-            if (rem < 32) v &= (1u << rem) - 1u;
+    for (int w = warp; w < a.W; w += kEfWarps) {
+        const uint32_t word = lane < nb ? a.X[(int64_t)(b0 + lane) * a.W + w] : 0u;
+        const int nv = min(32, a.N - 32 * w);
+        for (int t = 0; t < nv; ++t) {
+            const uint32_t m = __ballot_sync(0xffffffffu, (word >> t) & 1u);
+            if (lane == 0) cm[32 * w + t] = m;
         }
-        if (w == (N >> 5)) v |= 1u << (N & 31);
-        bits[q] = v;
     }
+    if (threadIdx.x == 0) cm[a.N] = 0xffffffffu;
     __syncthreads();
 
-    if (out_g) {
-        for (int j = warp; j < N; j += nwarps) {
-            float acc = 0.0f, comp = 0.0f;   // compensated (Kahan) sum
-            const int64_t e1 = fptr[j + 1];
-            for (int64_t e = fptr[j]; e < e1; ++e) {
-                const float c = fcoef[e];
-                uint32_t p = 1u;
-                for (int s = 0; s < KF; ++s) {
-                    const int v = fvars[e * KF + s];
-                    p &= bits[(v >> 5) * 32 + lane] >> (v & 31);
-                }
-                if (p & 1u) kahan_add(acc, comp, c);
-            }
-            if (FLIP && ((bits[(j >> 5) * 32 + lane] >> (j & 31)) & 1u)) acc = -acc;
-            gs[lane * NP + j] = acc;
+    if ((int)blockIdx.y < a.ES) {
+        const int64_t t0 = (int64_t)blockIdx.y * a.per_slice;
+        const int64_t t1 = min(a.M, t0 + a.per_slice);
+        const int64_t span = t1 > t0 ? t1 - t0 : 0;
+        const int64_t per_warp = ((span + kEfWarps - 1) / kEfWarps + 31) & ~(int64_t)31;
+        const int64_t w0 = min(t1, t0 + (int64_t)warp * per_warp);
+        const int64_t w1 = min(t1, w0 + per_warp);
+        const long long s = sum_active<ORDER, KS>(
+            cm, a.tvars, a.tfix, w0, w1, reinterpret_cast<typename VarRow<KS>::T*>(stv[warp]), stc[warp], lane);
+        red[warp][lane] = s;
+        __syncthreads();
+        if (warp == 0 && lane < nb) {
+            long long tot = 0;
+#pragma unroll
+            for (int q = 0; q < kEfWarps; ++q) tot += red[q][lane];
+            atomicAdd(a.acc + b0 + lane, (unsigned long long)tot);
         }
+        return;
     }
-
-    float eacc = 0.0f, ecomp = 0.0f;
-    for (int64_t t = warp; t < M; t += nwarps) {
-        const float c = tcoef[t];
-        uint32_t p = 1u;
-        for (int s = 0; s < K; ++s) {
-            const int v = tvars[t * KS + s];
-            p &= bits[(v >> 5) * 32 + lane] >> (v & 31);
-        }
-        if (p & 1u) kahan_add(eacc, ecomp, c);
-    }
-    red[warp * 32 + lane] = eacc;
-    __syncthreads();
-    if (warp == 0 && lane < nb) {
-        float e = 0.0f;
-        for (int q = 0; q < nwarps; ++q) e = __fadd_rn(e, red[q * 32 + lane]);
-        out_E[b0 + lane] = e;
-    }
-    if (out_g) {
-        for (int b = 0; b < nb; ++b)
-            for (int j = threadIdx.x; j < N; j += blockDim.x)
-                out_g[(int64_t)(b0 + b) * N + j] = gs[b * NP + j];
+    const int j = ((int)blockIdx.y - a.ES) * kEfWarps + warp;
+    if (j >= a.N) return;
+    const long long s = sum_active<KF, KV>(cm, a.fvars, a.ffix, a.fptr[j], a.fptr[j + 1],
+                                           reinterpret_cast<typename VarRow<KV>::T*>(stv[warp]), stc[warp],
+                                           lane);
+    if (lane < nb) {
+        float g = scalbnf(__ll2float_rn(s), -a.S);
+        if (a.flip && ((cm[j] >> lane) & 1u)) g = -g;
+        a.out_g[(int64_t)(b0 + lane) * a.N + j] = g;
     }
 }
 
-static size_t term_smem(int N, int W, bool with_g)
+__global__ void energy_fix_finalize_f32(const unsigned long long* __restrict__ acc, int B, int S,
+                                        float* __restrict__ E)
 {
-    return sizeof(uint32_t) * (size_t)(W + 1) * 32 + sizeof(float) * (kTermThreads / 32) * 32 +
-           (with_g ? sizeof(float) * 32 * (size_t)(N + 1) : 0);
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) E[b] = scalbnf(__ll2float_rn((long long)acc[b]), -S);
+}
+
+// Energies (into zeroed acc) and, with g, fields of B states.
+static cudaError_t launch_energy_fields(const hobo_instance* h, const uint32_t* X, int B, float* g, bool flip,
+                                        unsigned long long* acc, cudaStream_t st)
+{
+    if (B == 0) return cudaSuccess;
+    const auto& d = h->d;
+    const int tiles = (B + 31) / 32;
+    const int gslices = g ? (h->N + kEfWarps - 1) / kEfWarps : 0;
+    // energy blocks: enough to fill the GPU when there are no field blocks,
+    // else about as much work per block as a field block
+    int64_t ES;
+    if (g) {
+        const int64_t per_field_block = std::max<int64_t>(1, d.F * kEfWarps / std::max(h->N, 1));
+        ES = (d.M + per_field_block - 1) / per_field_block;
+    } else {
+        ES = std::min<int64_t>((4LL * h->num_sms + tiles - 1) / tiles, (d.M + 2047) / 2048);
+    }
+    ES = std::max<int64_t>(1, std::min<int64_t>(ES, 4096));
+    EfArgs a;
+    a.X = X; a.B = B; a.N = h->N; a.W = h->W;
+    a.tvars = d.tvars; a.tfix = d.tfix; a.M = d.M;
+    a.per_slice = (d.M + ES - 1) / ES;
+    a.ES = (int)ES;
+    a.fptr = d.fptr; a.fvars = d.fvars; a.ffix = d.ffix;
+    a.S = d.fix_shift; a.flip = flip ? 1 : 0; a.out_g = g; a.acc = acc;
+    const dim3 grid(tiles, (unsigned)(ES + gslices));
+    switch (h->order) {
+        case 1: energy_fields_kernel<1><<<grid, kEfThreads, 0, st>>>(a); break;
+        case 2: energy_fields_kernel<2><<<grid, kEfThreads, 0, st>>>(a); break;
+        case 3: energy_fields_kernel<3><<<grid, kEfThreads, 0, st>>>(a); break;
+        case 4: energy_fields_kernel<4><<<grid, kEfThreads, 0, st>>>(a); break;
+        case 5: energy_fields_kernel<5><<<grid, kEfThreads, 0, st>>>(a); break;
+        case 6: energy_fields_kernel<6><<<grid, kEfThreads, 0, st>>>(a); break;
+        case 7: energy_fields_kernel<7><<<grid, kEfThreads, 0, st>>>(a); break;
+        default: energy_fields_kernel<8><<<grid, kEfThreads, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_energy_terms(const hobo_instance* h, const uint32_t* X, int B, float* E,
                                 float* g_or_dE, bool flip_out, cudaStream_t st)
 {
     if (B == 0) return cudaSuccess;
-    const size_t sm = term_smem(h->N, h->W, g_or_dE != nullptr);
-    const unsigned grid = (unsigned)((B + 31) / 32);
-    const auto& d = h->d;
-    if (flip_out) {
-        cudaFuncSetAttribute(energy_terms_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        energy_terms_kernel<true><<<grid, kTermThreads, sm, st>>>(
-            X, B, h->N, h->W, d.fptr, d.fvars, d.fcoef, h->KF, d.tvars, d.tcoef32, d.M, h->order, h->KS,
-            g_or_dE, E);
-    } else {
-        cudaFuncSetAttribute(energy_terms_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        energy_terms_kernel<false><<<grid, kTermThreads, sm, st>>>(
-            X, B, h->N, h->W, d.fptr, d.fvars, d.fcoef, h->KF, d.tvars, d.tcoef32, d.M, h->order, h->KS,
-            g_or_dE, E);
+    unsigned long long* acc = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&acc, sizeof(unsigned long long) * (size_t)B, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)B, st);
+    if (e == cudaSuccess) e = launch_energy_fields(h, X, B, g_or_dE, flip_out, acc, st);
+    if (e == cudaSuccess) {
+        energy_fix_finalize_f32<<<(B + 255) / 256, 256, 0, st>>>(acc, B, h->d.fix_shift, E);
+        e = cudaGetLastError();
     }
-    return cudaGetLastError();
+    cudaFreeAsync(acc, st);
+    return e;
 }
 
 // ===========================================================================
-// float64 re-scoring.  Each folded coefficient is held as the 64-bit integer
-// round(c * 2^S), with S chosen per instance so that the sum of all
-// |coefficients| stays below 2^62; the energy of a state is the exact
-// integer sum of the coefficients of its active monomials, scaled by 2^-S
-// and rounded once to float64.  Integer instances are exact; otherwise the
-// error is at most (number of terms) * 2^-(S+1), below the rounding error of
-// a float64 summation of the same terms.  Blocks take 32 states (one per
-// lane) and a slice of the monomial list; slices are combined with 64-bit
-// integer atomics, whose result does not depend on their order.
+// float64 re-scoring: the same exact fixed-point energies, rounded once to
+// float64 (integer instances exact; otherwise the error is at most
+// (number of terms) * 2^-(S+1), below that of a float64 summation).
 // ===========================================================================
 constexpr int kFixThreads = 256;
-
-template <int KS>
-__global__ void __launch_bounds__(kFixThreads)
-energy_fix_kernel(const uint32_t* __restrict__ X, int B, int N, int W,
-                  const uint16_t* __restrict__ tvars, const long long* __restrict__ tfix,
-                  int64_t M, int64_t per_slice, unsigned long long* __restrict__ acc)
-{
-    using Row = typename std::conditional<KS == 4, uint2, uint4>::type;   // KS u16 slots
-    constexpr int U = 4;   // monomials in flight per warp
-    extern __shared__ uint32_t smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int b0 = blockIdx.x * 32;
-    const int nb = min(32, B - b0);
-    const int WS = W + 1;
-    uint32_t* bits = smem;
-    long long* red = reinterpret_cast<long long*>(bits + ((WS * 32 + 1) & ~1));
-    for (int q = threadIdx.x; q < WS * 32; q += blockDim.x) {
-        const int w = q >> 5, b = q & 31;
-        uint32_t v = 0;
-        if (w < W && b < nb) {
-            v = X[(int64_t)(b0 + b) * W + w];
-            const int rem = N - 32 * w;
-            if (rem < 32) v &= (1u << rem) - 1u;
-        }
-        if (w == (N >> 5)) v |= 1u << (N & 31);
-        bits[q] = v;
-    }
-    __syncthreads();
-    const int64_t t0 = (int64_t)blockIdx.y * per_slice;
-    const int64_t t1 = min(M, t0 + per_slice);
-    const Row* rows = reinterpret_cast<const Row*>(tvars);
-    long long s = 0;
-    for (int64_t t = t0 + (int64_t)warp * U; t < t1; t += (int64_t)nwarps * U) {
-        Row r[U];
-        long long c[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool ok = t + u < t1;
-            r[u] = ok ? __ldg(rows + t + u) : Row{};
-            c[u] = ok ? __ldg(tfix + t + u) : 0ll;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t* wv = reinterpret_cast<const uint32_t*>(&r[u]);
-            uint32_t p = 1u;
-#pragma unroll
-            for (int q = 0; q < KS / 2; ++q) {
-                const int v0 = wv[q] & 0xFFFFu, v1 = wv[q] >> 16;
-                p &= bits[(v0 >> 5) * 32 + lane] >> (v0 & 31);
-                p &= bits[(v1 >> 5) * 32 + lane] >> (v1 & 31);
-            }
-            if (p & 1u) s += c[u];
-        }
-    }
-    red[warp * 32 + lane] = s;
-    __syncthreads();
-    if (warp == 0 && lane < nb) {
-        long long tot = 0;
-        for (int q = 0; q < nwarps; ++q) tot += red[q * 32 + lane];
-        atomicAdd(acc + b0 + lane, (unsigned long long)tot);
-    }
-}
 
 // Dense order-3 instances: the same exact fixed-point sums, structured by
 // the dense layout.  Lanes are 32 states; warps take pairs (m, j), m < j.
@@ -307,69 +327,30 @@ __global__ void energy_fix_finalize(const unsigned long long* __restrict__ acc, 
     if (b < B) E[b] = ldexp((double)(long long)acc[b], -S);
 }
 
-cudaError_t launch_energy_fp64(const hobo_instance* h, const uint32_t* X, int B, double* E,
-                               cudaStream_t st)
-{
-    if (B == 0) return cudaSuccess;
-    const int64_t M = h->d.M;
-    const int tiles = (B + 31) / 32;
-    int slices = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * h->num_sms + tiles - 1) / tiles,
-                                                             (M + 4095) / 4096));
-    const int64_t per = (M + slices - 1) / std::max(slices, 1);
-    unsigned long long* acc = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&acc, sizeof(unsigned long long) * (size_t)B, st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)B, st);
-    if (e == cudaSuccess && h->d.C3fix) {
-        e = launch_fix_dense(h, X, B, acc, st);
-    } else if (e == cudaSuccess && M > 0) {
-        const size_t sm = sizeof(uint32_t) * (((size_t)(h->W + 1) * 32 + 1) & ~(size_t)1) +
-                          sizeof(long long) * (kFixThreads / 32) * 32;
-        if (h->KS == 4)
-            energy_fix_kernel<4><<<dim3(tiles, slices), kFixThreads, sm, st>>>(
-                X, B, h->N, h->W, h->d.tvars, h->d.tfix, M, per, acc);
-        else
-            energy_fix_kernel<8><<<dim3(tiles, slices), kFixThreads, sm, st>>>(
-                X, B, h->N, h->W, h->d.tvars, h->d.tfix, M, per, acc);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-        energy_fix_finalize<<<(B + 255) / 256, 256, 0, st>>>(acc, B, h->d.fix_shift, E);
-        e = cudaGetLastError();
-    }
-    cudaFreeAsync(acc, st);
-    return e;
-}
-
-// The same re-score with caller-owned accumulators: acc must hold B zeroed
-// 64-bit words on the device; nothing is allocated here.
 cudaError_t launch_energy_fp64_into(const hobo_instance* h, const uint32_t* X, int B, double* E,
                                     unsigned long long* acc, cudaStream_t st)
 {
     if (B == 0) return cudaSuccess;
-    const int64_t M = h->d.M;
-    const int tiles = (B + 31) / 32;
-    int slices = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * h->num_sms + tiles - 1) / tiles,
-                                                             (M + 4095) / 4096));
-    const int64_t per = (M + slices - 1) / std::max(slices, 1);
     cudaError_t e = cudaSuccess;
-    if (h->d.C3fix) {
-        e = launch_fix_dense(h, X, B, acc, st);
-    } else if (M > 0) {
-        const size_t sm = sizeof(uint32_t) * (((size_t)(h->W + 1) * 32 + 1) & ~(size_t)1) +
-                          sizeof(long long) * (kFixThreads / 32) * 32;
-        if (h->KS == 4)
-            energy_fix_kernel<4><<<dim3(tiles, slices), kFixThreads, sm, st>>>(
-                X, B, h->N, h->W, h->d.tvars, h->d.tfix, M, per, acc);
-        else
-            energy_fix_kernel<8><<<dim3(tiles, slices), kFixThreads, sm, st>>>(
-                X, B, h->N, h->W, h->d.tvars, h->d.tfix, M, per, acc);
-        e = cudaGetLastError();
-    }
+    if (h->d.C3fix) e = launch_fix_dense(h, X, B, acc, st);
+    else if (h->d.M > 0) e = launch_energy_fields(h, X, B, nullptr, false, acc, st);
     if (e == cudaSuccess) {
         energy_fix_finalize<<<(B + 255) / 256, 256, 0, st>>>(acc, B, h->d.fix_shift, E);
         e = cudaGetLastError();
     }
+    return e;
+}
+
+cudaError_t launch_energy_fp64(const hobo_instance* h, const uint32_t* X, int B, double* E,
+                               cudaStream_t st)
+{
+    if (B == 0) return cudaSuccess;
+    unsigned long long* acc = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&acc, sizeof(unsigned long long) * (size_t)B, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)B, st);
+    if (e == cudaSuccess) e = launch_energy_fp64_into(h, X, B, E, acc, st);
+    cudaFreeAsync(acc, st);
     return e;
 }
 

@@ -539,6 +539,9 @@ extern "C" int hobo_anneal_learned(hobo_h h, hobo_mlp_h m, uint64_t seed, int B,
     hobo_learned_opts o{};
     if (opts) o = *opts;
     if (o.plain_every == 0) o.plain_every = 4;
+    if (o.select != HOBO_SELECT_ORDER && o.select != HOBO_SELECT_THRESHOLD)
+        return mfail(HOBO_ERR_ARG, "select must be HOBO_SELECT_ORDER or HOBO_SELECT_THRESHOLD");
+    if (!std::isfinite(o.threshold)) return mfail(HOBO_ERR_ARG, "threshold must be finite");
     if (!(o.top_frac > 0.f)) o.top_frac = 1.f;
     if (o.top_frac > 1.f) o.top_frac = 1.f;
     if (o.table_size == 0) o.table_size = 1024;
@@ -589,6 +592,8 @@ extern "C" int hobo_anneal_learned(hobo_h h, hobo_mlp_h m, uint64_t seed, int B,
         L.vmax = o.vmax;
         L.plain_every = learned ? o.plain_every : 1;
         L.top_frac = o.top_frac;
+        L.select = o.select;
+        L.threshold = o.threshold;
         L.rec_every = record ? o.rec_every : 1;
         L.rec_states = record ? rec_states : 0;
         L.rec_F = record ? o.rec_F : nullptr;

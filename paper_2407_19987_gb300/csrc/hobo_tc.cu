@@ -413,7 +413,7 @@ energy_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams p)
                     e2 = __fadd_rn(e2, q);
                     e3 = __fadd_rn(e3, cacc);
                 }
-                if (b < B) p.out_g[(int64_t)b * N + m] = (p.flip && xm) ? -g : g;
+                if (b < B && p.out_g) p.out_g[(int64_t)b * N + m] = (p.flip && xm) ? -g : g;
             }
             float* dst = p.Epart + ((int64_t)c * kTcM + r) * 4;
             dst[0] = e1; dst[1] = e2; dst[2] = e3; dst[3] = 0.f;
@@ -493,7 +493,6 @@ cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, f
 {
     if (!tc_supported(h)) return cudaErrorNotSupported;
     if (B == 0) return cudaSuccess;
-    if (!g_or_dE) return cudaErrorNotSupported;   // the kernel always writes fields
     const auto& d = h->d;
     const int tiles = (B + kTcM - 1) / kTcM;
     const int chunks = std::max(1, std::min(h->N, h->num_sms / tiles));

@@ -370,11 +370,14 @@ inline cudaError_t run_batch(const SweepDev* descs, const int2* items, int nitem
 // ---------------------------------------------------------------------------
 // Learned-proposal sweep.  In a learned sweep each state scores its bits
 // with the network's per-sweep score table (a function of the scaled field
-// and the bit), orders them by descending score (ties by index) and attempts
-// the first ceil(top_frac * N) of them, 32 at a time, with the same
-// Metropolis test and random words as the plain sweep; every plain_every-th
-// sweep is a plain sweep over all bits in index order (with plain_every <= 1
-// every sweep is plain and the trajectories equal the tuned kernel's).
+// and the bit) at the start of the sweep, then either orders them by
+// descending score (ties by index; a bitonic sort of (score, index) keys
+// held in registers, 32*WMAX keys per warp) and attempts the first
+// ceil(top_frac * N), or attempts the bits whose score is >= threshold in
+// index order.  Attempts go 32 at a time with the same Metropolis test and
+// random words as the plain sweep; every plain_every-th sweep is a plain
+// sweep over all bits in index order (with plain_every <= 1 every sweep is
+// plain and the trajectories equal the tuned kernel's).
 // Optionally records, for states b < rec_states and sweeps s with
 // s % rec_every == 0, the features of every attempted bit at its decision:
 // (clamp(beta*g, +-vmax)/8, 2x-1, -ln(beta)/4) and the bit itself.
@@ -384,7 +387,9 @@ struct LearnedDev {
     int G;
     float vmax;
     int plain_every;
+    int select;            // 0: descending score, top_frac; 1: score >= threshold
     float top_frac;
+    float threshold;
     int rec_every, rec_states;
     float* rec_F;          // [n_rec_sweeps][rec_states][N][3]
     uint8_t* rec_x;        // [n_rec_sweeps][rec_states][N]
@@ -393,6 +398,55 @@ struct LearnedDev {
 __host__ __device__ constexpr int learned_region_floats(int N, int WMAX)
 {
     return 2 * ((N + 3) & ~3) + 4 * (WMAX + 1) + 8 + ((N + 3) & ~3) + (((N + 3) & ~3) / 2 + 4);
+}
+
+// Score of a bit from the sweep's table: linear interpolation over the
+// clamped scaled field, row x of the table.
+__device__ __forceinline__ float learned_score(const float* tab, const LearnedDev& L, float scale, float bg,
+                                               uint32_t xi)
+{
+    const float v = fminf(fmaxf(bg, -L.vmax), L.vmax);
+    const float pos = (v + L.vmax) * scale;
+    const int k = min((int)pos, L.G - 2);
+    const float fr = pos - (float)k;
+    const float* t = tab + xi * L.G;
+    return fmaf(fr, t[k + 1] - t[k], t[k]);
+}
+
+// Bitonic sort of 32*E keys into descending order; key r of a lane is
+// element r*32 + lane.  Strides below 32 exchange between lanes, larger
+// ones between registers of a lane.
+template <int E>
+__device__ __forceinline__ void bitonic_desc(uint64_t (&key)[E], int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int rj = j >> 5;
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    if (r & rj) continue;
+                    const int r2 = r | rj;
+                    const bool desc = ((r * 32 + lane) & k) == 0;
+                    const uint64_t a = key[r], b = key[r2];
+                    if ((a < b) == desc) { key[r] = b; key[r2] = a; }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const uint64_t o = __shfl_xor_sync(0xffffffffu, key[r], j);
+                    const bool desc = ((r * 32 + lane) & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    const bool take_max = lower == desc;
+                    const uint64_t mx = key[r] > o ? key[r] : o;
+                    const uint64_t mn = key[r] > o ? o : key[r];
+                    key[r] = take_max ? mx : mn;
+                }
+            }
+        }
+    }
 }
 
 template <int WMAX, bool DENSE, int KU>
@@ -443,27 +497,45 @@ __device__ __forceinline__ void anneal_state_learned(const SweepDev& p, const Le
         if (!plain) {
             const float* tab = L.tables + (size_t)s * 2 * L.G;
             const float scale = (float)(L.G - 1) / (2.f * L.vmax);
-            for (int i = lane; i < N; i += 32) {
-                const float v = fminf(fmaxf(beta * g[i], -L.vmax), L.vmax);
-                const int xi = (sel_word(x, i >> 5) >> (i & 31)) & 1u;
-                const float pos = (v + L.vmax) * scale;
-                const int k = min((int)pos, L.G - 2);
-                const float fr = pos - (float)k;
-                const float* t = tab + xi * L.G;
-                score[i] = fmaf(fr, t[k + 1] - t[k], t[k]);
-            }
-            __syncwarp();
-            for (int i = lane; i < N; i += 32) {
-                const float si = score[i];
-                int rank = 0;
-                for (int j = 0; j < N; ++j) {
-                    const float sj = score[j];
-                    rank += (sj > si || (sj == si && j < i)) ? 1 : 0;
+            if (L.select == 0) {
+                // keys: order-preserving bits of the score (+0 for -0), then
+                // 0xFFFF - i so that equal scores put the lower index first;
+                // padding keys are 0, below every real key
+                uint64_t key[WMAX];
+#pragma unroll
+                for (int r = 0; r < WMAX; ++r) {
+                    const int i = r * 32 + lane;
+                    key[r] = 0ull;
+                    if (i < N) {
+                        const float sc = learned_score(tab, L, scale, beta * g[i],
+                                                       (sel_word(x, i >> 5) >> (i & 31)) & 1u) + 0.0f;
+                        uint32_t u = __float_as_uint(sc);
+                        u ^= (u & 0x80000000u) ? 0xFFFFFFFFu : 0x80000000u;
+                        key[r] = ((uint64_t)u << 32) | (uint64_t)(0xFFFFu - (uint32_t)i);
+                    }
                 }
-                order[rank] = (uint16_t)i;
+                bitonic_desc<WMAX>(key, lane);
+#pragma unroll
+                for (int r = 0; r < WMAX; ++r) {
+                    const int p = r * 32 + lane;
+                    if (p < N) order[p] = (uint16_t)(0xFFFFu - (uint32_t)(key[r] & 0xFFFFu));
+                }
+                nvisit = max(1, min(N, (int)ceilf(L.top_frac * (float)N)));
+            } else {
+                int base = 0;
+                for (int k0 = 0; k0 < N; k0 += 32) {
+                    const int i = k0 + lane;
+                    bool take = false;
+                    if (i < N)
+                        take = learned_score(tab, L, scale, beta * g[i], (sel_word(x, i >> 5) >> (i & 31)) & 1u) >=
+                               L.threshold;
+                    const uint32_t m = __ballot_sync(0xffffffffu, take);
+                    if (take) order[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
+                    base += __popc(m);
+                }
+                nvisit = base;
             }
             __syncwarp();
-            nvisit = max(1, min(N, (int)ceilf(L.top_frac * (float)N)));
         }
         for (int k0 = 0; k0 < nvisit; k0 += 32) {
             const int kk = k0 + lane;

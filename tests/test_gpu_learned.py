@@ -152,17 +152,26 @@ CASES = [
 ]
 
 
+# (plain_every, select, top_frac, threshold).  With the identity network the
+# score is clamp(beta g)/8; on integer instances distinct scores differ by
+# at least beta/8, far above the table interpolation's rounding, and no
+# score lies within that rounding of the thresholds -1e-3 and 0.3, so the
+# interpolated scores order and select exactly as the oracle's.
+SELECTS = [(3, 0, 1.0, 0.0), (4, 0, 0.6, 0.0), (2, 0, 0.1, 0.0), (3, 1, 1.0, -1e-3), (2, 1, 1.0, 0.3)]
+
+
 @pytest.mark.parametrize("name,maker,flags,B,sched", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("plain_every,top_frac", [(3, 1.0), (4, 0.6), (2, 0.1)])
-def test_learned_anneal_matches_oracle(name, maker, flags, B, sched, plain_every, top_frac):
+@pytest.mark.parametrize("plain_every,select,top_frac,threshold", SELECTS)
+def test_learned_anneal_matches_oracle(name, maker, flags, B, sched, plain_every, select, top_frac, threshold):
     inst = maker()
     betas = W.geometric_betas(*sched)
     h = gpuh.make(inst, flags)
     w = identity_net()
     m = _set_net(w)
-    r = _H().anneal_learned(h, m, 77, B, betas, plain_every=plain_every, top_frac=top_frac,
-                            want_final=True, want_accepts=True)
-    ref = O.anneal_learned(inst, 77, B, betas, w, plain_every=plain_every, top_frac=top_frac)
+    r = _H().anneal_learned(h, m, 77, B, betas, plain_every=plain_every, select=select, top_frac=top_frac,
+                            threshold=threshold, want_final=True, want_accepts=True)
+    ref = O.anneal_learned(inst, 77, B, betas, w, plain_every=plain_every, select=select, top_frac=top_frac,
+                           threshold=threshold)
     _compare(r, ref, inst.N)
     h.close()
 
@@ -193,10 +202,11 @@ def test_recorded_features_and_labels_match_oracle():
     h = gpuh.make(inst)
     w = identity_net()
     m = _set_net(w)
-    for net in (None, m):
-        r = _H().anneal_learned(h, net, 31, 40, betas, plain_every=3, top_frac=0.5, rec_every=5, rec_states=7)
+    for net, sel in ((None, 0), (m, 0), (m, 1)):
+        r = _H().anneal_learned(h, net, 31, 40, betas, plain_every=3, select=sel, top_frac=0.5, threshold=-1e-3,
+                                rec_every=5, rec_states=7)
         ref = O.anneal_learned(inst, 31, 40, betas, w if net is not None else None, plain_every=3,
-                               top_frac=0.5, rec_every=5, rec_B=7)
+                               select=sel, top_frac=0.5, threshold=-1e-3, rec_every=5, rec_B=7)
         F = r["rec_F"].cpu().numpy()
         np.testing.assert_array_equal(r["rec_y"].cpu().numpy(), ref["rec_y"])
         np.testing.assert_array_equal(F[:, :2], ref["rec_F"][:, :2])
@@ -215,6 +225,8 @@ def test_learned_anneal_arguments():
         _H().anneal_learned(h, None, 1, 8, W.geometric_betas(5, .1, 4))   # N > 256
     h.close()
     h = gpuh.make(W.tiny_dense(1))
+    with pytest.raises(_H().HoboError):
+        _H().anneal_learned(h, None, 1, 8, W.geometric_betas(5, .1, 4), select=2)
     r = _H().anneal_learned(h, None, 1, 0, W.geometric_betas(5, .1, 4))
     assert r["bestE"].numel() == 0
     r = _H().anneal_learned(h, None, 1, 16, np.zeros(0, np.float32), want_final=True)

@@ -157,3 +157,29 @@ def test_learned_anneal_energies_are_consistent():
     assert np.array_equal(r["E"], O.energy(inst, r["X"]))
     assert np.array_equal(r["bestE"], O.energy(inst, r["bestX"]))
     assert np.all(r["bestE"] <= r["E"])
+
+
+def test_threshold_sweep_attempts_bits_at_or_above_threshold():
+    # select 1: one learned sweep attempts exactly the bits whose score
+    # (here clamp(beta g)/8) is >= threshold at the start state
+    inst = WL.sparse_order4(seed=5005, N=40, density=0.05)
+    N, B = inst.N, 5
+    beta = np.array([0.3], np.float32)
+    X0 = O.init_states(8, N, B)
+    for thr in (-0.2, 0.0, 0.4):
+        r = O.anneal_learned(inst, 8, B, beta, identity_net(), plain_every=2, select=1, threshold=thr,
+                             vmax=20.0, rec_every=1, rec_B=B)
+        for b in range(B):
+            g = O.fields(inst, X0[b]).astype(np.float32)
+            v = np.clip(beta[0] * g, -20.0, 20.0) / 8
+            got = set(np.nonzero(r["rec_x"][b * N:(b + 1) * N] != 0xFF)[0])
+            assert got == set(np.nonzero(v >= thr)[0])
+
+
+def test_threshold_below_every_score_is_plain_anneal():
+    inst = WL.tiny_dense()
+    b = _sched(inst, 30)
+    a = O.anneal(inst, 4, 6, b)
+    l = O.anneal_learned(inst, 4, 6, b, identity_net(), plain_every=3, select=1, threshold=-1e9)
+    for k in ("X", "E", "bestX", "bestE", "accepts"):
+        assert np.array_equal(a[k], l[k]), k
