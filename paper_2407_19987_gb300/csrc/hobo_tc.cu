@@ -17,7 +17,8 @@
 // Roles (192 threads): warp 0 issues TMA loads of the coefficient slabs
 // (128-byte swizzle, 4-stage ring), warp 1 issues the MMAs (one thread),
 // warps 2-5 read the accumulators (double-buffered, 2 x 256 columns) and
-// run the epilogue.  All threads expand the state bits of a tile into the
+// run the epilogue; the quadratic parts q_bm come from a small pre-pass
+// (pair_fields_kernel).  All threads expand the state bits of a tile into the
 // bf16 A operand in shared memory.  CTA c owns state tile c % T and a chunk
 // of the variables m; tiles advance through m in step.  Every wait on an mbarrier gives up
 // after kWaitNs and reports HOBO_ERR_TIMEOUT through the status word.
@@ -30,14 +31,14 @@ namespace hobo {
 
 constexpr int kTcM = 128;          // states per tile (MMA M)
 constexpr int kTcKB = 64;          // K elements per swizzle atom (128 bytes)
-constexpr int kTcStages = 4;
+constexpr int kTcStages = 5;
 constexpr int kTcThreads = 192;
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s
 
 struct TcParams {
     const uint32_t* X;
     int B, N, W, NJ, KP, nsplit, P;
-    const float* S2;
+    const float* Qt;     // [N][B] quadratic parts q_bm, from pair_fields_kernel
     const float* a;
     float* out_g;
     int flip;
@@ -192,7 +193,6 @@ energy_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams p)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
     volatile int* never_set = abort_flag + 1;     // stays 0: teardown waits use only the time limit
 
-    float* s2row = reinterpret_cast<float*>(tmem_holder + 4);   // [4 warps][NJ] staged pair-matrix rows
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = p.N, W = p.W, B = p.B;
     const int c = blockIdx.x;
@@ -343,32 +343,11 @@ energy_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams p)
             }
             float e1 = 0.f, e2 = 0.f, e3 = 0.f;
             const int nch = (p.NJ + 31) / 32;   // columns >= N meet zero bits
-            const int SP = (p.NJ + 31) & ~31;          // staged row pitch, zero padded
-            float* srow = s2row + (warp - 2) * SP;       // this warp's copy
             for (int j = it; j < seg_end; ++j) {
                 const int m = j % N;
                 const int buf = acc_epi & 1;
-                __syncwarp();
-                for (int q2 = lane; q2 < SP; q2 += 32) srow[q2] = q2 < N ? __ldg(p.S2 + (int64_t)m * p.P + q2) : 0.f;
-                __syncwarp();
-                // quadratic part: sum of the staged row m over set bits, four
-                // independent partial sums (x * v with x in {0,1} is exact)
-                float q0 = 0.f, q1 = 0.f, q2s = 0.f, q3 = 0.f;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    if (32 * k >= SP) break;
-                    const uint32_t xw = x[k];
-                    const float4* r4 = reinterpret_cast<const float4*>(srow + 32 * k);
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        const float4 v = r4[t];
-                        q0 = fmaf((float)((xw >> (4 * t)) & 1u), v.x, q0);
-                        q1 = fmaf((float)((xw >> (4 * t + 1)) & 1u), v.y, q1);
-                        q2s = fmaf((float)((xw >> (4 * t + 2)) & 1u), v.z, q2s);
-                        q3 = fmaf((float)((xw >> (4 * t + 3)) & 1u), v.w, q3);
-                    }
-                }
-                const float q = __fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2s, q3));
+                // quadratic part, from the pair pre-pass
+                const float q = b < B ? __ldg(p.Qt + (int64_t)m * B + b) : 0.f;
                 // the warp leaves together: tcgen05.ld below needs all 32 lanes
                 const bool ok = __all_sync(0xffffffffu, mbar_wait(&afull[buf], ((uint32_t)acc_epi >> 1) & 1u, abort_flag));
                 if (!ok) {
@@ -389,12 +368,14 @@ energy_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams p)
                     const uint32_t xw = xr[0];
 #pragma unroll
                     for (int k = 0; k < 7; ++k) xr[k] = xr[k + 1];
+                    // add the accumulator of column j where bit j is set (the
+                    // same value as x * D + c with x in {0, 1})
 #pragma unroll
                     for (int t = 0; t < 32; t += 4) {
-                        c0 = fmaf((float)((xw >> t) & 1u), __uint_as_float(v[t]), c0);
-                        c1 = fmaf((float)((xw >> (t + 1)) & 1u), __uint_as_float(v[t + 1]), c1);
-                        c2 = fmaf((float)((xw >> (t + 2)) & 1u), __uint_as_float(v[t + 2]), c2);
-                        c3 = fmaf((float)((xw >> (t + 3)) & 1u), __uint_as_float(v[t + 3]), c3);
+                        if ((xw >> t) & 1u) c0 = __fadd_rn(c0, __uint_as_float(v[t]));
+                        if ((xw >> (t + 1)) & 1u) c1 = __fadd_rn(c1, __uint_as_float(v[t + 1]));
+                        if ((xw >> (t + 2)) & 1u) c2 = __fadd_rn(c2, __uint_as_float(v[t + 2]));
+                        if ((xw >> (t + 3)) & 1u) c3 = __fadd_rn(c3, __uint_as_float(v[t + 3]));
                     }
                 }
                 const float cacc = __fadd_rn(__fadd_rn(c0, c1), __fadd_rn(c2, c3));
@@ -435,6 +416,56 @@ energy_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams p)
     }
 }
 
+// Quadratic parts of the fields for the tensor-core epilogue:
+// Qt[m][b] = q_bm = sum_j x_bj S2[m][j], as four partial sums over the
+// columns j = 4t + u (u = 0..3), added (0 + 1) + (2 + 3).  A block takes 128
+// states (one per thread) and a chunk of rows m, staged in shared memory.
+constexpr int kPairThreads = 128;
+
+__global__ void __launch_bounds__(kPairThreads)
+pair_fields_kernel(const uint32_t* __restrict__ X, int B, int N, int W, const float* __restrict__ S2, int P,
+                   int mchunk, float* __restrict__ Qt)
+{
+    __shared__ float4 row[64];
+    const int b = blockIdx.x * kPairThreads + threadIdx.x;
+    uint32_t x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        uint32_t v = (b < B && k < W) ? X[(int64_t)b * W + k] : 0u;
+        const int rem = N - 32 * k;
+        if (rem <= 0) v = 0u; else if (rem < 32) v &= (1u << rem) - 1u;
+        x[k] = v;
+    }
+    const int P4 = P >> 2;
+    const int m0 = blockIdx.y * mchunk, m1 = min(N, m0 + mchunk);
+    for (int m = m0; m < m1; ++m) {
+        __syncthreads();
+        if (threadIdx.x < P4) row[threadIdx.x] = __ldg(reinterpret_cast<const float4*>(S2 + (int64_t)m * P) + threadIdx.x);
+        __syncthreads();
+        float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+        uint32_t xr[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) xr[k] = x[k];
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+            if (8 * k >= P4) break;
+            const uint32_t xw = xr[0];
+#pragma unroll
+            for (int k2 = 0; k2 < 7; ++k2) xr[k2] = xr[k2 + 1];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                if (8 * k + t >= P4) break;
+                const float4 v = row[8 * k + t];
+                q0 = fmaf((float)((xw >> (4 * t)) & 1u), v.x, q0);
+                q1 = fmaf((float)((xw >> (4 * t + 1)) & 1u), v.y, q1);
+                q2 = fmaf((float)((xw >> (4 * t + 2)) & 1u), v.z, q2);
+                q3 = fmaf((float)((xw >> (4 * t + 3)) & 1u), v.w, q3);
+            }
+        }
+        if (b < B) Qt[(int64_t)m * B + b] = __fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, q3));
+    }
+}
+
 // E_b from the partial sums of the m-chunks of its tile, added in chunk
 // order: E = sum x_m a_m + 1/2 sum x_m q_m + 1/6 sum x_m (2 c_m).
 __global__ void energy_tc_finalize(const float* __restrict__ Epart, int B, int T, int chunks,
@@ -455,8 +486,7 @@ __global__ void energy_tc_finalize(const float* __restrict__ Epart, int B, int T
 
 static size_t tc_smem_bytes(int NJ, int KP)
 {
-    return 1024 + (size_t)(KP / kTcKB) * 16384 + (size_t)kTcStages * NJ * 128 + 256 +
-           4 * 4 * (size_t)((NJ + 31) & ~31);
+    return 1024 + (size_t)(KP / kTcKB) * 16384 + (size_t)kTcStages * NJ * 128 + 256;
 }
 
 bool tc_supported(const hobo_instance* h)
@@ -499,14 +529,26 @@ cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, f
     const int G = tiles * chunks;
     TcParams p{};
     p.X = X; p.B = B; p.N = h->N; p.W = h->W; p.NJ = d.NJ; p.KP = d.KP; p.nsplit = d.nsplit;
-    p.P = (h->N + 3) & ~3; p.S2 = d.S2; p.a = d.a; p.out_g = g_or_dE; p.flip = flip_out ? 1 : 0;
+    p.P = (h->N + 3) & ~3; p.a = d.a; p.out_g = g_or_dE; p.flip = flip_out ? 1 : 0;
     p.T = tiles; p.chunks = chunks; p.G = G; p.status = h->status;
     float* Epart = nullptr;
+    float* Qt = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&Epart, sizeof(float) * (size_t)G * kTcM * 4, st);
     if (e != cudaSuccess) return e;
+    e = cudaMallocAsync((void**)&Qt, sizeof(float) * (size_t)h->N * B, st);
+    if (e != cudaSuccess) { cudaFreeAsync(Epart, st); return e; }
     p.Epart = Epart;
+    p.Qt = Qt;
+    {
+        const int btiles = (B + kPairThreads - 1) / kPairThreads;
+        const int mch = std::max(1, std::min(h->N, (2 * h->num_sms + btiles - 1) / btiles));
+        const int mchunk = (h->N + mch - 1) / mch;
+        pair_fields_kernel<<<dim3(btiles, (h->N + mchunk - 1) / mchunk), kPairThreads, 0, st>>>(
+            X, B, h->N, h->W, d.S2, p.P, mchunk, Qt);
+        e = cudaGetLastError();
+    }
     const size_t sm = tc_smem_bytes(d.NJ, d.KP);
-    e = cudaFuncSetAttribute(energy_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(energy_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess) {
         const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(d.tmap);
         energy_tc_kernel<<<G, kTcThreads, sm, st>>>(*map, p);
@@ -517,6 +559,7 @@ cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, f
         e = cudaGetLastError();
     }
     cudaFreeAsync(Epart, st);
+    cudaFreeAsync(Qt, st);
     return e;
 }
 
