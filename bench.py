@@ -40,7 +40,7 @@ WORKLOAD = "dense_float"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="tuned", choices=["tuned", "plain"])
@@ -195,7 +195,9 @@ def run_ours(a):
     h = H.Instance.from_terms(inst.idx, inst.coef, inst.N)
     info = h.info()
     mode = H.HOBO_ANNEAL_TUNED if a.mode == "tuned" else H.HOBO_ANNEAL_PLAIN
-    seed = 2 + 1_000_003 * rank          # each rank anneals its own B states (weak scaling)
+    # each rank anneals its own B states, global states [rank*B, (rank+1)*B)
+    # of one seeded batch (weak scaling; no collective on the data path)
+    seed, state0 = 2, rank * B
     W_ = h.W
     bestX = torch.zeros((B, W_), dtype=torch.int32, device=dev)
     bestE32 = torch.empty(B, dtype=torch.float32, device=dev)
@@ -204,7 +206,7 @@ def run_ours(a):
 
     def step(events=None, accepts=False):
         return h.anneal(seed, B, betas, mode=mode, bestX=bestX, bestE32=bestE32,
-                        want_accepts=accepts, want_bytes=accepts, sweep_events=events)
+                        want_accepts=accepts, want_bytes=accepts, sweep_events=events, state0=state0)
 
     for _ in range(a.warmup):
         step()
@@ -252,7 +254,7 @@ def run_ours(a):
     for k in range(max(2, a.steps)):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        rr = h.anneal(seed, B, pin_beta.numpy(), mode=mode, bestX=bestX, bestE32=bestE32)
+        rr = h.anneal(seed, B, pin_beta.numpy(), mode=mode, bestX=bestX, bestE32=bestE32, state0=state0)
         hX.copy_(rr["bestX"], non_blocking=True)
         hE.copy_(rr["bestE"], non_blocking=True)
         torch.cuda.synchronize()
@@ -260,6 +262,11 @@ def run_ours(a):
     e2e_v = world * flips_step / (statistics.mean(e2e_ms) / 1000.0)
     h2d = betas.nbytes
     d2h = hX.numel() * 4 + hE.numel() * 8
+    # the one exchange of the multi-GPU form, after the timed region: the
+    # ranks agree on the overall best state (lowest energy, lowest index)
+    from paper_2407_19987_gb300.sharded import global_best, local_best
+    bE, bidx, bk = local_best(hE.numpy(), state0)
+    gE, gidx, _ = global_best(bE, bidx, hX.numpy()[bk], W_, device=dev if world > 1 else None)
 
     pk, pk_kind = peaks()
     # DRAM bytes (read + write) of one full-size launch of the dense sweep
@@ -284,6 +291,7 @@ def run_ours(a):
                    "mode": a.mode, "dense_layout": info["dense"], "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": f"replicas x{world} (independent states per GPU)",
                    "accepted_flips_per_step": accepts, "sweep_coef_bytes_per_step": coef_bytes,
+                   "best_energy": gE, "best_state_index": gidx,
                    "sweep_kernel_ms": sweep_avg},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": sweep_dram_bytes if a.mode == "tuned" else None,

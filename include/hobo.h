@@ -194,6 +194,10 @@ typedef struct {
     void* ev_sweep_begin;  /* cudaEvent_t or NULL: recorded on `stream` right
                               before the sweep kernel is enqueued */
     void* ev_sweep_end;    /* cudaEvent_t or NULL: recorded right after it */
+    uint64_t state0;       /* global index of state 0 of this call: the random
+                              streams of state b are those of state state0 + b,
+                              so calls on disjoint index ranges (e.g. one per
+                              GPU) reproduce one call on the whole range */
 } hobo_anneal_opts;
 
 /*
@@ -202,7 +206,8 @@ typedef struct {
  *   seed    64-bit key of the counter-based Philox4x32-10 stream.  The draw
  *           for (state b, sweep s, bit i) uses counter (i/4, s, b, 0),
  *           word i%4; initial bit i of state b uses counter (i/4, 0, b, 1),
- *           bit 31 of word i%4.  Results do not depend on the launch shape.
+ *           bit 31 of word i%4 (b offset by opts->state0, taken mod 2^32).
+ *           Results do not depend on the launch shape.
  *   beta    host float32 [sweeps], inverse temperature of each sweep.
  *   Each sweep visits bits 0..N-1 in order; a flip with delta dE is
  *   accepted iff dE <= 0 or u < exp2(-(beta*dE)*log2 e), u = (w>>8)*2^-24,

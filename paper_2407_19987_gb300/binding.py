@@ -74,7 +74,7 @@ class hobo_anneal_opts(C.Structure):
     _fields_ = [("mode", C.c_int), ("states_per_block", C.c_int), ("sweep0", C.c_int),
                 ("resume", C.c_int), ("X_io", C.c_void_p), ("bestE32_io", C.c_void_p),
                 ("E_io", C.c_void_p), ("g_io", C.c_void_p), ("accepts", C.c_void_p), ("coef_bytes", C.c_void_p), ("ev_sweep_begin", C.c_void_p),
-                ("ev_sweep_end", C.c_void_p)]
+                ("ev_sweep_end", C.c_void_p), ("state0", C.c_uint64)]
 
 
 _lib = None
@@ -245,8 +245,9 @@ class Instance:
                states_per_block: int = 0, sweep0: int = 0, resume: bool = False, X=None,
                bestX=None, bestE32=None, E=None, g=None, want_final: bool = False,
                want_fields: bool = False, want_accepts: bool = False, want_bytes: bool = False,
-               device=None, stream=None, sweep_events=None) -> dict:
-        """Batched annealing (hobo_anneal).  betas: host float32 [sweeps].
+               device=None, stream=None, sweep_events=None, state0: int = 0) -> dict:
+        """Batched annealing (hobo_anneal).  betas: host float32 [sweeps];
+        state0: global index of the first state (random streams).
         Returns a dict of CUDA tensors: bestX [B, W] int32, bestE [B] f64, and
         when asked X (final), E (final f32), bestE32, accepts."""
         import torch
@@ -272,7 +273,8 @@ class Instance:
                     e.record()
             ev0, ev1 = sweep_events[0].cuda_event, sweep_events[1].cuda_event
         o = hobo_anneal_opts(mode, states_per_block, sweep0, 1 if resume else 0,
-                             _ptr(X), _ptr(bestE32), _ptr(E), _ptr(g), _ptr(acc), _ptr(cb), ev0, ev1)
+                             _ptr(X), _ptr(bestE32), _ptr(E), _ptr(g), _ptr(acc), _ptr(cb), ev0, ev1,
+                             int(state0) & (2 ** 64 - 1))
         _check(load_library().hobo_anneal(self._h, C.c_uint64(seed & (2 ** 64 - 1)), B,
                                           betas.ctypes.data_as(C.c_void_p), betas.shape[0],
                                           _ptr(bestX), _ptr(bestE), C.byref(o), _stream(stream)))

@@ -87,12 +87,12 @@ constexpr uint32_t kStreamInit = 1u;
 
 // Word w of the initial state b: bit i is bit 31 of word (i % 4) of the
 // Philox block with counter (i / 4, 0, b, 1); bits >= N are zero.
-__device__ __forceinline__ uint32_t init_word(int b, int w, int N, uint32_t k0, uint32_t k1)
+__device__ __forceinline__ uint32_t init_word(uint32_t b, int w, int N, uint32_t k0, uint32_t k1)
 {
     uint32_t word = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const u32x4 r = philox10((uint32_t)(8 * w + q), 0u, (uint32_t)b, kStreamInit, k0, k1);
+        const u32x4 r = philox10((uint32_t)(8 * w + q), 0u, b, kStreamInit, k0, k1);
         word |= ((r.a >> 31) << (4 * q)) | ((r.b >> 31) << (4 * q + 1)) |
                 ((r.c >> 31) << (4 * q + 2)) | ((r.d >> 31) << (4 * q + 3));
     }

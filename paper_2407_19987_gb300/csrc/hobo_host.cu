@@ -635,7 +635,7 @@ int hobo_anneal(hobo_h h, uint64_t seed, int B, const float* beta, int sweeps, u
     if (o.E_io) d_E = o.E_io;
     else ACHECK(cudaMallocAsync((void**)&d_E, sizeof(float) * (size_t)B, st), "cudaMallocAsync E");
 
-    if (!o.resume) ACHECK(launch_init_states(d_X, B, N, W, seed, st), "init states");
+    if (!o.resume) ACHECK(launch_init_states(d_X, B, N, W, seed, st, (uint32_t)o.state0), "init states");
     if (!(o.resume && o.g_io && o.E_io)) {
         rc = hobo::energy_dispatch(h, d_X, B, d_E, d_g, false, 0, st);
         if (rc != HOBO_OK) { cleanup(); return rc; }
@@ -643,6 +643,7 @@ int hobo_anneal(hobo_h h, uint64_t seed, int B, const float* beta, int sweeps, u
 
     SweepArgs a;
     a.B = B; a.sweeps = sweeps; a.sweep0 = o.sweep0; a.resume = o.resume; a.seed = seed;
+    a.state0 = (uint32_t)o.state0;
     a.S = o.states_per_block;
     a.beta = d_beta; a.X = d_X; a.g = d_g; a.E = d_E; a.bestX = bestX; a.bestE = d_bE;
     a.accepts = o.accepts;

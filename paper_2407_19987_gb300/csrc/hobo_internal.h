@@ -84,7 +84,8 @@ struct hobo_instance {
 namespace hobo {
 
 // ---- kernel launchers (hobo_kernels.cu / hobo_tc.cu) ---------------------
-cudaError_t launch_init_states(uint32_t* X, int B, int N, int W, uint64_t seed, cudaStream_t st);
+cudaError_t launch_init_states(uint32_t* X, int B, int N, int W, uint64_t seed, cudaStream_t st,
+                               uint32_t state0 = 0);
 
 // g_or_dE: [B][N] or null; flip_out: write (1-2x)g instead of g
 cudaError_t launch_energy_terms(const hobo_instance* h, const uint32_t* X, int B, float* E,
@@ -99,6 +100,7 @@ cudaError_t launch_energy_fp64_into(const hobo_instance* h, const uint32_t* X, i
 struct SweepArgs {
     int B = 0, sweeps = 0, sweep0 = 0, resume = 0, S = 32;
     uint64_t seed = 0;
+    uint32_t state0 = 0;           // global index of state 0 (Philox counter offset)
     const float* beta = nullptr;   // device [sweeps]
     uint32_t* X = nullptr;         // device [B][W] in: start states, out: final
     float* g = nullptr;            // device [B][N] in: fields of X (plain: in/out)

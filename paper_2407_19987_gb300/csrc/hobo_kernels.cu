@@ -14,21 +14,22 @@ namespace hobo {
 // Philox(counter = (i/4, 0, b, 1), key = seed).
 // ===========================================================================
 __global__ void init_states_kernel(uint32_t* __restrict__ X, int B, int N, int W,
-                                   uint32_t k0, uint32_t k1)
+                                   uint32_t k0, uint32_t k1, uint32_t state0)
 {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= (int64_t)B * W) return;
     const int b = (int)(tid / W), w = (int)(tid % W);
-    X[tid] = init_word(b, w, N, k0, k1);
+    X[tid] = init_word(state0 + (uint32_t)b, w, N, k0, k1);
 }
 
-cudaError_t launch_init_states(uint32_t* X, int B, int N, int W, uint64_t seed, cudaStream_t st)
+cudaError_t launch_init_states(uint32_t* X, int B, int N, int W, uint64_t seed, cudaStream_t st,
+                               uint32_t state0)
 {
     if (B == 0) return cudaSuccess;
     const int64_t n = (int64_t)B * W;
     const int threads = 256;
     init_states_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
-        X, B, N, W, (uint32_t)seed, (uint32_t)(seed >> 32));
+        X, B, N, W, (uint32_t)seed, (uint32_t)(seed >> 32), state0);
     return cudaGetLastError();
 }
 
@@ -385,7 +386,7 @@ __global__ void sweep_plain_kernel(const SweepDev p)
         const uint32_t sw = (uint32_t)(p.sweep0 + s);
         for (int i = 0; i < N; ++i) {
             if ((i & 3) == 0)
-                r = philox10((uint32_t)(i >> 2), sw, (uint32_t)b, kStreamMetropolis, p.k0, p.k1);
+                r = philox10((uint32_t)(i >> 2), sw, p.state0 + (uint32_t)b, kStreamMetropolis, p.k0, p.k1);
             const uint32_t xi = bit_of(x, i);
             const float gi = g[i];
             const float dE = xi ? -gi : gi;
@@ -450,6 +451,7 @@ SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
     p.N = h->N; p.W = h->W; p.B = a.B; p.sweeps = a.sweeps; p.sweep0 = a.sweep0;
     p.resume = a.resume; p.P = (h->N + 3) & ~3;
     p.k0 = (uint32_t)a.seed; p.k1 = (uint32_t)(a.seed >> 32);
+    p.state0 = a.state0;
     p.beta = a.beta; p.X = a.X; p.g = a.g; p.E = a.E; p.bestX = a.bestX; p.bestE = a.bestE;
     p.accepts = a.accepts;
     p.coef_bytes = a.coef_bytes;

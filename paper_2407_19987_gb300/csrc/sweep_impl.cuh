@@ -22,6 +22,7 @@ struct SweepDev {
     int N, W, B, sweeps, sweep0, resume, P;   // P: row pitch of the dense slab
     int write_g;
     uint32_t k0, k1;
+    uint32_t state0;     // global index of state 0 (Philox counter offset)
     const float* beta;
     uint32_t* X;
     float* g;
@@ -260,7 +261,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
             // lane t of word w' then takes its block from lane
             // 8 * (w' - w0) + t / 4.
             if ((w & 3) == 0)
-                r4 = philox10((uint32_t)(8 * w + lane), sw, (uint32_t)b, kStreamMetropolis, p.k0, p.k1);
+                r4 = philox10((uint32_t)(8 * w + lane), sw, p.state0 + (uint32_t)b, kStreamMetropolis, p.k0, p.k1);
             const int src = 8 * (w & 3) + (lane >> 2);
             const uint32_t ra = __shfl_sync(0xffffffffu, r4.a, src);
             const uint32_t rb = __shfl_sync(0xffffffffu, r4.b, src);
@@ -541,7 +542,7 @@ __device__ __forceinline__ void anneal_state_learned(const SweepDev& p, const Le
             const int kk = k0 + lane;
             const bool valid = kk < nvisit;
             const int i = valid ? (plain ? kk : (int)order[kk]) : 0;
-            const u32x4 r4 = philox10((uint32_t)(i >> 2), sw, (uint32_t)b, kStreamMetropolis, p.k0, p.k1);
+            const u32x4 r4 = philox10((uint32_t)(i >> 2), sw, p.state0 + (uint32_t)b, kStreamMetropolis, p.k0, p.k1);
             const uint32_t rw = pick4(r4, i & 3);
             int t0 = 0;
             while (true) {

@@ -181,3 +181,23 @@ def test_dense_float_full_size_best_energies():
     e32 = r["bestE32"].cpu().numpy().astype(np.float64)
     absi = gpuh.abs_instance(inst)
     assert gpuh.rel_err(e32[sample], bestE[sample], O.energy(absi, bx)).max() <= 1e-4
+
+
+@pytest.mark.parametrize("maker,flags", [(lambda: W.tiny_dense(1), 0), (lambda: W.dense_float(2, N=64), 0),
+                                         (lambda: W.sparse_order4(5003), 0)], ids=["tiny", "dense64", "order4"])
+@pytest.mark.parametrize("mode", [TUNED, PLAIN])
+def test_state_offset_shards_reproduce_one_call(maker, flags, mode):
+    """Shards of the state range, each with its global offset, give the
+    results of one call on the whole range (the multi-GPU split)."""
+    inst = maker()
+    betas = W.geometric_betas(5.0, 0.05, 25)
+    h = gpuh.make(inst, flags)
+    full = _run(h, 9, 70, betas, mode)
+    T = gpuh.torch()
+    parts = [_run(h, 9, hi - lo, betas, mode, state0=lo) for lo, hi in ((0, 33), (33, 70))]
+    for k in ("bestX", "bestE", "X", "E", "accepts"):
+        assert T.equal(T.cat([p[k] for p in parts]), full[k]), k
+    if inst.integer:
+        ref = O.anneal(inst, 9, 37, betas, state0=33)
+        np.testing.assert_array_equal(parts[1]["bestE"].cpu().numpy(), ref["bestE"])
+    h.close()
