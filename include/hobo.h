@@ -233,6 +233,17 @@ int hobo_anneal(hobo_h h, uint64_t seed, int B, const float* beta, int sweeps,
  */
 int hobo_check(hobo_h h, void* stream);
 
+/*
+ * hobo_selftest_timeout -- diagnostic of the timeout path (no counterpart in
+ * the paper): enqueues on `stream` a one-thread kernel that waits, through
+ * the same bounded mbarrier wait as the contraction kernel, on a barrier
+ * that nothing completes.  After limit_ns (1 .. 1e9 ns) the wait gives up
+ * and records the timeout in h's status word, so the next hobo_check
+ * returns HOBO_ERR_TIMEOUT (and clears it).  The GPU context stays usable.
+ * Errors: HOBO_ERR_ARG (NULL h, limit out of range), HOBO_ERR_CUDA.
+ */
+int hobo_selftest_timeout(hobo_h h, uint64_t limit_ns, void* stream);
+
 /* ---- batches of instances ---------------------------------------------- */
 
 /*

@@ -99,6 +99,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     L.hobo_energy_fp64.argtypes = [P, P, I, P, P]
     L.hobo_anneal.argtypes = [P, U64, I, P, I, P, P, C.POINTER(hobo_anneal_opts), P]
     L.hobo_check.argtypes = [P, P]
+    L.hobo_selftest_timeout.argtypes = [P, U64, P]
+    L.hobo_selftest_timeout.restype = I
     L.hobo_energy_fp64_noalloc.argtypes = [P, P, I, P, P]
     L.hobo_energy_fp64_noalloc.restype = I
     L.hobo_batch_create.argtypes = [C.POINTER(P), P, I, P]
@@ -222,6 +224,11 @@ class Instance:
         """Synchronize the stream and raise HoboError(HOBO_ERR_TIMEOUT) if a
         kernel of this instance gave up a bounded wait."""
         _check(load_library().hobo_check(self._h, _stream(stream)))
+
+    def selftest_timeout(self, limit_ns: int = 10_000_000, stream=None):
+        """hobo_selftest_timeout: a bounded device wait that runs out; the
+        next check() raises HoboError(HOBO_ERR_TIMEOUT)."""
+        _check(load_library().hobo_selftest_timeout(self._h, C.c_uint64(limit_ns), _stream(stream)))
 
     def energy_fp64_noalloc(self, X, E=None, stream=None):
         """hobo_energy_fp64_noalloc: float64 re-score using the library's fixed

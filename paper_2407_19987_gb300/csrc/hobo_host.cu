@@ -542,6 +542,15 @@ int hobo_check(hobo_h h, void* stream)
     return HOBO_OK;
 }
 
+int hobo_selftest_timeout(hobo_h h, uint64_t limit_ns, void* stream)
+{
+    if (!h) return fail(HOBO_ERR_ARG, "NULL instance");
+    if (limit_ns == 0 || limit_ns > 1000000000ull) return fail(HOBO_ERR_ARG, "limit_ns must be 1..1e9");
+    cudaError_t e = launch_wait_timeout_selftest(h, limit_ns, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "timeout self-test");
+    return HOBO_OK;
+}
+
 int hobo_info(hobo_h h, hobo_info_t* info)
 {
     if (!h || !info) return fail(HOBO_ERR_ARG, "NULL argument");

@@ -120,6 +120,7 @@ cudaError_t launch_sweep_plain(const hobo_instance* h, const SweepArgs& a, cudaS
 cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, float* E,
                              float* g_or_dE, bool flip_out, cudaStream_t st);
 bool tc_supported(const hobo_instance* h);
+cudaError_t launch_wait_timeout_selftest(const hobo_instance* h, uint64_t limit_ns, cudaStream_t st);
 cudaError_t make_tc_tensor_map(hobo_instance* h);
 
 void set_error(const std::string& msg);

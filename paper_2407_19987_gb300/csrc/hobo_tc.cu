@@ -88,15 +88,16 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Bounded wait: false after kWaitNs or once another thread has aborted.
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag)
+// Bounded wait: false after limit_ns or once another thread has aborted.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                       uint64_t limit_ns = kWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -464,6 +465,27 @@ pair_fields_kernel(const uint32_t* __restrict__ X, int B, int N, int W, const fl
         }
         if (b < B) Qt[(int64_t)m * B + b] = __fadd_rn(__fadd_rn(q0, q1), __fadd_rn(q2, q3));
     }
+}
+
+// Timeout self-test: one thread waits, through the same bounded wait as the
+// contraction kernel, on an mbarrier that nothing arrives at; when the
+// limit runs out it records the timeout in the instance's status word the
+// way the contraction kernel does.
+__global__ void wait_timeout_selftest_kernel(int* status, uint64_t limit_ns)
+{
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0u, &abort_flag, limit_ns)) set_abort(&abort_flag, status);
+}
+
+cudaError_t launch_wait_timeout_selftest(const hobo_instance* h, uint64_t limit_ns, cudaStream_t st)
+{
+    wait_timeout_selftest_kernel<<<1, 32, 0, st>>>(h->status, limit_ns);
+    return cudaGetLastError();
 }
 
 // E_b from the partial sums of the m-chunks of its tile, added in chunk

@@ -200,3 +200,24 @@ def test_check_reports_no_timeout_after_normal_work():
     h = gpuh.make(inst)
     h.energy(gpuh.to_dev(W.random_states(2, 64, inst.N)))
     h.check()
+
+
+def test_bounded_wait_timeout_is_reported_and_context_survives():
+    """A bounded device wait on a barrier nothing completes gives up after
+    its limit; hobo_check reports HOBO_ERR_TIMEOUT once, and the context
+    keeps working (the contraction afterwards matches the oracle)."""
+    import paper_2407_19987_gb300 as H
+    inst = W.dense_float(100, 64)
+    h = gpuh.make(inst)
+    h.selftest_timeout(20_000_000)
+    with pytest.raises(H.HoboError) as ei:
+        h.check()
+    assert ei.value.code == H.HOBO_ERR_TIMEOUT
+    h.check()                                   # status cleared
+    X = W.random_states(3, 16, inst.N)
+    E, _ = h.energy(gpuh.to_dev(X))
+    ref = O.energy(inst, X)
+    assert np.all(gpuh.rel_err(E.cpu().numpy().astype(np.float64), ref, O.energy(gpuh.abs_instance(inst), X))
+                  <= gpuh.FLOAT_RTOL)
+    with pytest.raises(H.HoboError):
+        h.selftest_timeout(0)
