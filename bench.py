@@ -303,8 +303,9 @@ def run_ours(a):
                             "peak_from": "ncu lts__t_bytes.sum.peak_sustained x L2 clock"}},
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         # per step: initial states, pair pre-pass, tensor-core contraction +
-        # its finalize, sweep, exact re-score + its finalize
-        "gpu_launches": 7 * a.steps,
+        # its finalize, sweep, exact re-score (pair part, limb contraction,
+        # finalize)
+        "gpu_launches": 8 * a.steps,
         "wall_s_timed": wall,
     }
     cl = cs.summary()

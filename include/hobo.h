@@ -61,6 +61,9 @@ extern "C" {
                                  1e-5 bar on ill-conditioned fields).  Integer
                                  coefficients below 2^16 always use hi+lo,
                                  which is exact for them. */
+#define HOBO_RESCORE_CUDA_CORES 32u  /* float64 re-score of dense instances on
+                                 CUDA cores only (no limb planes for the
+                                 exact tensor-core re-score; same results) */
 
 typedef struct hobo_instance* hobo_h;
 

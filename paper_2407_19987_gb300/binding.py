@@ -29,6 +29,7 @@ HOBO_FORCE_SPARSE = 2
 HOBO_FORCE_DENSE = 4
 HOBO_SPLIT3 = 8
 HOBO_SPLIT2 = 16
+HOBO_RESCORE_CUDA_CORES = 32
 
 HOBO_ANNEAL_TUNED = 0
 HOBO_ANNEAL_PLAIN = 1

@@ -93,7 +93,7 @@ static int upload(T** dst, const std::vector<T>& src)
 static void free_layouts(DevLayouts& d)
 {
     void* ptrs[] = {d.tvars, d.tfix, d.fptr, d.fvars, d.ffix, d.cptr, d.chdr,
-                    d.ltgt, d.lcnt, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf,
+                    d.ltgt, d.lcnt, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf, d.S3limb, d.rs_a, d.rs_S2,
                     d.C3fix, d.S2fix, d.afix, d.pair_m, d.pair_j};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -124,6 +124,61 @@ static double choose_split(double c, int nsplit, uint16_t out[3])
         r -= (double)bf16_value(out[q]);
     }
     return r;   // residual not represented
+}
+
+// bf16 bits of a small integer (|v| <= 256: exact in bf16)
+static uint16_t bf16_of_small_int(int v)
+{
+    const float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+}
+
+// Limb planes of the fixed-point cubic coefficients for the exact
+// tensor-core re-score (layout in DevLayouts).  Left out (the CUDA-core
+// re-score stays in use) when a partial sum could leave 62 bits.
+static int build_exact_limbs(hobo_instance* h, const std::vector<Entry>& mono)
+{
+    DevLayouts& d = h->d;
+    const int N = h->N;
+    const int S = h->integer ? 0 : d.fix_shift;
+    long long maxC = 0;
+    double sumC = 0.0;
+    for (auto& e : mono) {
+        const long long f = std::llrint(std::ldexp(e.c, S));
+        maxC = std::max(maxC, f < 0 ? -f : f);
+        sumC += std::fabs((double)f);
+    }
+    if (sumC >= 4.0e18 || (double)maxC * N * N >= 4.0e18) return HOBO_OK;
+    int L = 1;
+    while (L < 8 && maxC >= (1LL << (8 * L - 1))) ++L;
+    const size_t plane = (size_t)N * d.NJ * d.KP;
+    std::vector<uint16_t> limbs(plane * L, 0);
+    std::vector<long long> ra((size_t)N, 0), rs2((size_t)N * N, 0);
+    for (auto& e : mono) {
+        const long long f = std::llrint(std::ldexp(e.c, S));
+        if (e.m.d == 1) ra[e.m.v[0]] = f;
+        else if (e.m.d == 2) rs2[(size_t)e.m.v[0] * N + e.m.v[1]] = f;
+        else {
+            const uint64_t u = (uint64_t)f;
+            const size_t at = ((size_t)e.m.v[0] * d.NJ + e.m.v[1]) * d.KP + e.m.v[2];
+            for (int q = 0; q < L; ++q) {
+                int limb = (int)((u >> (8 * q)) & 0xFFu);
+                if (q == L - 1 && limb >= 128) limb -= 256;     // signed top limb
+                limbs[q * plane + at] = bf16_of_small_int(limb);
+            }
+        }
+    }
+    int rc;
+    if ((rc = upload(&d.S3limb, limbs)) || (rc = upload(&d.rs_a, ra)) || (rc = upload(&d.rs_S2, rs2))) return rc;
+    d.rs_L = L;
+    d.rs_shift = S;
+    if (make_tc_tensor_map_rs(h) != cudaSuccess) {
+        (void)cudaGetLastError();
+        d.tmap_rs_ok = false;
+    }
+    return HOBO_OK;
 }
 
 // Build every layout from the folded monomial list (sorted by degree, then
@@ -292,6 +347,7 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
                 (void)cudaGetLastError();
                 d.tmap_ok = false;
             }
+            if (!(flags & HOBO_RESCORE_CUDA_CORES) && (rc = build_exact_limbs(h, mono))) return rc;
         }
     } else {
         // (3) update lists grouped by (flipped bit i, target j)

@@ -65,6 +65,18 @@ struct DevLayouts {
     int nsplit = 0, NJ = 0, KP = 0;
     alignas(64) unsigned char tmap[128] = {};   // CUtensorMap of the planes
     bool tmap_ok = false;
+    // exact re-score on the tensor cores (N <= 256): the fixed-point cubic
+    // coefficients C[m][j][l] = round(c * 2^rs_shift), m < j < l (else 0),
+    // as rs_L signed 8-bit limbs (C = sum_q limb_q 2^(8q), limbs below the
+    // top unsigned), each limb an exact bf16 plane [rs_L][N][NJ][KP]; linear
+    // and pair coefficients at the same scale.  rs_shift = 0 for integer
+    // instances, fix_shift otherwise (the same integers as C3fix).
+    uint16_t* S3limb = nullptr;
+    long long* rs_a = nullptr;    // [N]
+    long long* rs_S2 = nullptr;   // [N][N], m < j
+    int rs_L = 0, rs_shift = 0;
+    alignas(64) unsigned char tmap_rs[128] = {};
+    bool tmap_rs_ok = false;
 };
 
 }  // namespace hobo
@@ -120,8 +132,12 @@ cudaError_t launch_sweep_plain(const hobo_instance* h, const SweepArgs& a, cudaS
 cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, float* E,
                              float* g_or_dE, bool flip_out, cudaStream_t st);
 bool tc_supported(const hobo_instance* h);
+bool exact_tc_supported(const hobo_instance* h);
 cudaError_t launch_wait_timeout_selftest(const hobo_instance* h, uint64_t limit_ns, cudaStream_t st);
 cudaError_t make_tc_tensor_map(hobo_instance* h);
+cudaError_t make_tc_tensor_map_rs(hobo_instance* h);
+cudaError_t launch_energy_exact_tc(const hobo_instance* h, const uint32_t* X, int B, unsigned long long* acc,
+                                   cudaStream_t st);
 
 void set_error(const std::string& msg);
 

@@ -333,10 +333,17 @@ cudaError_t launch_energy_fp64_into(const hobo_instance* h, const uint32_t* X, i
 {
     if (B == 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    if (h->d.C3fix) e = launch_fix_dense(h, X, B, acc, st);
-    else if (h->d.M > 0) e = launch_energy_fields(h, X, B, nullptr, false, acc, st);
+    int shift = h->d.fix_shift;
+    if (exact_tc_supported(h)) {
+        e = launch_energy_exact_tc(h, X, B, acc, st);
+        shift = h->d.rs_shift;
+    } else if (h->d.C3fix) {
+        e = launch_fix_dense(h, X, B, acc, st);
+    } else if (h->d.M > 0) {
+        e = launch_energy_fields(h, X, B, nullptr, false, acc, st);
+    }
     if (e == cudaSuccess) {
-        energy_fix_finalize<<<(B + 255) / 256, 256, 0, st>>>(acc, B, h->d.fix_shift, E);
+        energy_fix_finalize<<<(B + 255) / 256, 256, 0, st>>>(acc, B, shift, E);
         e = cudaGetLastError();
     }
     return e;

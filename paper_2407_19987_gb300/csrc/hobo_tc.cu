@@ -516,7 +516,7 @@ bool tc_supported(const hobo_instance* h)
     return h->dense && h->d.S3bf && h->d.tmap_ok && h->N <= 256;
 }
 
-cudaError_t make_tc_tensor_map(hobo_instance* h)
+static cudaError_t encode_planes_map(void* map_out, const void* base, int planes, int N, int NJ, int KP)
 {
     using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -525,19 +525,355 @@ cudaError_t make_tc_tensor_map(hobo_instance* h)
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
-    const auto& d = h->d;
-    cuuint64_t dims[2] = {(cuuint64_t)d.KP, (cuuint64_t)d.nsplit * h->N * d.NJ};
-    cuuint64_t strides[1] = {(cuuint64_t)d.KP * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kTcKB, (cuuint32_t)d.NJ};
+    cuuint64_t dims[2] = {(cuuint64_t)KP, (cuuint64_t)planes * N * NJ};
+    cuuint64_t strides[1] = {(cuuint64_t)KP * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTcKB, (cuuint32_t)NJ};
     cuuint32_t estr[2] = {1, 1};
-    CUtensorMap* map = reinterpret_cast<CUtensorMap*>(h->d.tmap);
-    CUresult r = reinterpret_cast<EncodeFn>(fn)(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)d.S3bf, dims,
-                                                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    h->d.tmap_ok = true;
-    return cudaSuccess;
+    CUresult r = reinterpret_cast<EncodeFn>(fn)(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                                                2, const_cast<void*>(base), dims, strides, box, estr,
+                                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t make_tc_tensor_map(hobo_instance* h)
+{
+    const auto& d = h->d;
+    cudaError_t e = encode_planes_map(h->d.tmap, d.S3bf, d.nsplit, h->N, d.NJ, d.KP);
+    h->d.tmap_ok = e == cudaSuccess;
+    return e;
+}
+
+cudaError_t make_tc_tensor_map_rs(hobo_instance* h)
+{
+    const auto& d = h->d;
+    cudaError_t e = encode_planes_map(h->d.tmap_rs, d.S3limb, d.rs_L, h->N, d.NJ, d.KP);
+    h->d.tmap_rs_ok = e == cudaSuccess;
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// Exact re-score on the tensor cores.  The fixed-point cubic coefficients
+// C[m][j][l] (m < j < l) are split into rs_L signed 8-bit limbs, one bf16
+// plane each (exact), and for a tile of 128 states each item (m, q) forms
+// D_q[b][j] = sum_l limb_q[m][j][l] x_bl on the tensor cores.  Every term is
+// an integer of magnitude <= 255 and K <= 256, so D_q is an exact integer
+// below 2^24 in float32, and so is s_q = sum_j x_bj D_q[b][j] (at most 256
+// such terms in four partial sums).  The epilogue adds x_bm * s_q * 2^(8q)
+// to a 64-bit accumulator: the cubic energy sum_{m<j<l} C x_m x_j x_l
+// exactly, the same integer as the CUDA-core re-score.  K blocks and
+// accumulator columns that hold only zeros (l <= m + 1, j <= m) are
+// skipped; items with no K block left are skipped by all three roles.
+// ---------------------------------------------------------------------------
+struct TcExactParams {
+    const uint32_t* X;
+    int B, N, W, NJ, KP, L;
+    int T, chunks, G;
+    unsigned long long* acc;
+    int* status;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+energy_tc_exact_kernel(const __grid_constant__ CUtensorMap tmap, const TcExactParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int nKB = p.KP / kTcKB;
+    const uint32_t stage_bytes = (uint32_t)p.NJ * 128u;
+    uint8_t* sA = smem;
+    uint8_t* sB = sA + nKB * 16384;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kTcStages * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kTcStages;
+    uint64_t* afull = bars + 2 * kTcStages;
+    uint64_t* aempty = afull + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(aempty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+    volatile int* never_set = abort_flag + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = p.N, W = p.W, B = p.B;
+    const int c = blockIdx.x;
+    const int tile_c = c % p.T, chunk = c / p.T;
+    const int i0 = tile_c * N + (int)((int64_t)chunk * N / p.chunks);
+    const int i1 = tile_c * N + (int)((int64_t)(chunk + 1) * N / p.chunks);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&afull[s], 1);
+            mbar_init(&aempty[s], 4);
+        }
+        *abort_flag = 0;
+        *never_set = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    int pstage = 0;
+    uint32_t pphase = 0;
+    uint32_t armed_phase[kTcStages];
+    bool armed[kTcStages];
+    for (int s = 0; s < kTcStages; ++s) { armed[s] = false; armed_phase[s] = 0; }
+    int cstage = 0;
+    uint32_t cphase = 0;
+    int acc_mma = 0, acc_epi = 0;
+    const uint32_t idesc = idesc_bf16(kTcM, p.NJ);
+
+    for (int it = i0; it < i1;) {
+        const int tile = it / N;
+        const int seg_end = min(i1, (tile + 1) * N);
+        {
+            const int cpr = p.KP / 8;
+            for (int q = threadIdx.x; q < kTcM * cpr; q += blockDim.x) {
+                const int r = q / cpr, cc = q % cpr;
+                const int kb = cc >> 3, ch = cc & 7;
+                const int b = tile * kTcM + r;
+                const int l0 = cc * 8;
+                uint32_t byte = 0;
+                if (b < B && l0 < N) {
+                    byte = (p.X[(int64_t)b * W + (l0 >> 5)] >> (l0 & 31)) & 0xFFu;
+                    const int rem = N - l0;
+                    if (rem < 8) byte &= (1u << rem) - 1u;
+                }
+                uint32_t wv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t lo = ((byte >> (2 * e)) & 1u) ? 0x3F80u : 0u;
+                    const uint32_t hi = ((byte >> (2 * e + 1)) & 1u) ? 0x3F80u : 0u;
+                    wv[e] = lo | (hi << 16);
+                }
+                uint8_t* dst = sA + kb * 16384 + (r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4);
+                *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+
+        if (warp == 0) {
+            if (lane == 0) {
+                for (int j = it; j < seg_end && !*abort_flag; ++j) {
+                    const int m = j % N;
+                    const int kb0 = (m + 2) / kTcKB;     // l >= m + 2 only
+                    if (kb0 >= nKB) continue;
+                    for (int q = 0; q < p.L; ++q)
+                        for (int kb = kb0; kb < nKB; ++kb) {
+                            if (!mbar_wait(&empty[pstage], pphase ^ 1u, abort_flag)) {
+                                set_abort(abort_flag, p.status);
+                                break;
+                            }
+                            mbar_expect_tx(&full[pstage], stage_bytes);
+                            tma_load_2d(sB + pstage * stage_bytes, &tmap, kb * kTcKB, (q * N + m) * p.NJ,
+                                        &full[pstage]);
+                            armed[pstage] = true;
+                            armed_phase[pstage] = pphase;
+                            if (++pstage == kTcStages) { pstage = 0; pphase ^= 1u; }
+                        }
+                }
+            }
+        } else if (warp == 1) {
+            if (lane == 0) {
+                bool ok = true;
+                for (int j = it; j < seg_end && ok && !*abort_flag; ++j) {
+                    const int m = j % N;
+                    const int kb0 = (m + 2) / kTcKB;
+                    if (kb0 >= nKB) continue;
+                    for (int q = 0; q < p.L && ok; ++q) {
+                        const int buf = acc_mma & 1;
+                        if (!mbar_wait(&aempty[buf], (((uint32_t)acc_mma >> 1) & 1u) ^ 1u, abort_flag)) {
+                            set_abort(abort_flag, p.status);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d = tmem + (uint32_t)(buf * 256);
+                        uint32_t accum = 0;
+                        for (int kb = kb0; kb < nKB; ++kb) {
+                            if (!mbar_wait(&full[cstage], cphase, abort_flag)) {
+                                set_abort(abort_flag, p.status);
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t a0 = smem_u32(sA + kb * 16384);
+                            const uint32_t b0 = smem_u32(sB + cstage * stage_bytes);
+#pragma unroll
+                            for (int k = 0; k < kTcKB / 16; ++k) {
+                                tc_mma(d, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), idesc, accum);
+                                accum = 1;
+                            }
+                            tc_commit(&empty[cstage]);
+                            if (++cstage == kTcStages) { cstage = 0; cphase ^= 1u; }
+                        }
+                        if (!ok) break;
+                        tc_commit(&afull[buf]);
+                        ++acc_mma;
+                    }
+                }
+            }
+        } else {
+            const int quad = warp & 3;
+            const int r = quad * 32 + lane;
+            const int b = tile * kTcM + r;
+            uint32_t x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                uint32_t v = (b < B && k < W) ? p.X[(int64_t)b * W + k] : 0u;
+                const int rem = N - 32 * k;
+                if (rem <= 0) v = 0u; else if (rem < 32) v &= (1u << rem) - 1u;
+                x[k] = v;
+            }
+            long long e3 = 0;
+            const int nch = (p.NJ + 31) / 32;
+            bool ok = true;
+            for (int j = it; j < seg_end && ok; ++j) {
+                const int m = j % N;
+                const int kb0 = (m + 2) / kTcKB;
+                if (kb0 >= nKB) continue;
+                uint32_t xmw = x[0];
+#pragma unroll
+                for (int k = 1; k < 8; ++k) xmw = ((m >> 5) == k) ? x[k] : xmw;
+                const bool xm = (xmw >> (m & 31)) & 1u;
+                const int ch0 = (m + 1) >> 5;             // columns j <= m hold zeros
+                for (int q = 0; q < p.L; ++q) {
+                    const int buf = acc_epi & 1;
+                    ok = __all_sync(0xffffffffu, mbar_wait(&afull[buf], ((uint32_t)acc_epi >> 1) & 1u, abort_flag));
+                    if (!ok) {
+                        if (lane == 0) set_abort(abort_flag, p.status);
+                        break;
+                    }
+                    tc_fence_after();
+                    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+                    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256);
+#pragma unroll 1
+                    for (int ch = ch0; ch < nch; ++ch) {
+                        uint32_t v[32];
+                        tmem_ld32(tbase + (uint32_t)(ch * 32), v);
+                        tmem_ld_wait();
+                        uint32_t xw = x[0];
+#pragma unroll
+                        for (int k = 1; k < 8; ++k) xw = (ch == k) ? x[k] : xw;
+#pragma unroll
+                        for (int t = 0; t < 32; t += 4) {
+                            if ((xw >> t) & 1u) c0 = __fadd_rn(c0, __uint_as_float(v[t]));
+                            if ((xw >> (t + 1)) & 1u) c1 = __fadd_rn(c1, __uint_as_float(v[t + 1]));
+                            if ((xw >> (t + 2)) & 1u) c2 = __fadd_rn(c2, __uint_as_float(v[t + 2]));
+                            if ((xw >> (t + 3)) & 1u) c3 = __fadd_rn(c3, __uint_as_float(v[t + 3]));
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&aempty[buf]);
+                    ++acc_epi;
+                    if (xm) {
+                        const long long sq = __float2ll_rn(__fadd_rn(__fadd_rn(c0, c1), __fadd_rn(c2, c3)));
+                        e3 += sq * (1LL << (8 * q));
+                    }
+                }
+            }
+            if (b < B && e3 != 0) atomicAdd(p.acc + b, (unsigned long long)e3);
+        }
+        __syncthreads();
+        it = seg_end;
+    }
+
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        for (int s = 0; s < kTcStages; ++s)
+            if (armed[s]) (void)mbar_wait(&full[s], armed_phase[s], never_set);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// Exact linear and pair parts: acc[b] += sum_m x_bm (a[m] + sum_{j>m} x_bj S2[m][j])
+// in 64-bit fixed point.  A block takes 128 states and a chunk of rows m.
+__global__ void __launch_bounds__(kPairThreads)
+pair_exact_kernel(const uint32_t* __restrict__ X, int B, int N, int W, const long long* __restrict__ a,
+                  const long long* __restrict__ S2, int mchunk, unsigned long long* __restrict__ acc)
+{
+    __shared__ long long row[256];
+    const int b = blockIdx.x * kPairThreads + threadIdx.x;
+    uint32_t x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        uint32_t v = (b < B && k < W) ? X[(int64_t)b * W + k] : 0u;
+        const int rem = N - 32 * k;
+        if (rem <= 0) v = 0u; else if (rem < 32) v &= (1u << rem) - 1u;
+        x[k] = v;
+    }
+    long long s = 0;
+    const int m0 = blockIdx.y * mchunk, m1 = min(N, m0 + mchunk);
+    for (int m = m0; m < m1; ++m) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < N; j += kPairThreads) row[j] = __ldg(S2 + (int64_t)m * N + j);
+        __syncthreads();
+        uint32_t xmw = x[0];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) xmw = ((m >> 5) == k) ? x[k] : xmw;
+        if (!((xmw >> (m & 31)) & 1u)) continue;
+        long long t = __ldg(a + m);
+#pragma unroll 1
+        for (int k = (m + 1) >> 5; k < W; ++k) {
+            uint32_t xw = x[0];
+#pragma unroll
+            for (int k2 = 1; k2 < 8; ++k2) xw = (k == k2) ? x[k2] : xw;
+            if (32 * k <= m) xw &= ~((2u << (m & 31)) - 1u);   // j > m only
+#pragma unroll 4
+            for (int u = 0; u < 32; ++u)
+                if ((xw >> u) & 1u) t += row[32 * k + u];
+        }
+        s += t;
+    }
+    if (b < B && s != 0) atomicAdd(acc + b, (unsigned long long)s);
+}
+
+bool exact_tc_supported(const hobo_instance* h)
+{
+    return h->dense && h->d.S3limb && h->d.tmap_rs_ok && h->N <= 256;
+}
+
+// acc (B zeroed words) += exact fixed-point energies (scale 2^rs_shift)
+cudaError_t launch_energy_exact_tc(const hobo_instance* h, const uint32_t* X, int B, unsigned long long* acc,
+                                   cudaStream_t st)
+{
+    if (!exact_tc_supported(h)) return cudaErrorNotSupported;
+    if (B == 0) return cudaSuccess;
+    const auto& d = h->d;
+    {
+        const int btiles = (B + kPairThreads - 1) / kPairThreads;
+        const int mch = std::max(1, std::min(h->N, (2 * h->num_sms + btiles - 1) / btiles));
+        const int mchunk = (h->N + mch - 1) / mch;
+        pair_exact_kernel<<<dim3(btiles, (h->N + mchunk - 1) / mchunk), kPairThreads, 0, st>>>(
+            X, B, h->N, h->W, d.rs_a, d.rs_S2, mchunk, acc);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int tiles = (B + kTcM - 1) / kTcM;
+    const int chunks = std::max(1, std::min(h->N, h->num_sms / tiles));
+    TcExactParams p{};
+    p.X = X; p.B = B; p.N = h->N; p.W = h->W; p.NJ = d.NJ; p.KP = d.KP; p.L = d.rs_L;
+    p.T = tiles; p.chunks = chunks; p.G = tiles * chunks; p.acc = acc; p.status = h->status;
+    const size_t sm = tc_smem_bytes(d.NJ, d.KP);
+    cudaError_t e = cudaFuncSetAttribute(energy_tc_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(d.tmap_rs);
+    energy_tc_exact_kernel<<<p.G, kTcThreads, sm, st>>>(*map, p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g_or_dE,

@@ -221,3 +221,44 @@ def test_bounded_wait_timeout_is_reported_and_context_survives():
                   <= gpuh.FLOAT_RTOL)
     with pytest.raises(H.HoboError):
         h.selftest_timeout(0)
+
+
+@pytest.mark.parametrize("N,B,integer", [(12, 300, True), (33, 129, False), (64, 300, True), (200, 257, False),
+                                         (256, 4096, False)])
+def test_exact_tensor_core_rescore_equals_cuda_core_rescore(N, B, integer):
+    """The float64 re-score on the tensor cores (8-bit limb planes of the
+    fixed-point coefficients) gives exactly the CUDA-core re-score's
+    values: both round the same exact integer once; integer instances also
+    equal the oracle's int64 energies."""
+    import paper_2407_19987_gb300 as H
+    inst = W.random_sparse(70 + N, N, 3, 0.6, "int") if integer else W.dense_float(71, N)
+    X = W.random_states(72, B, N)
+    Xd = gpuh.to_dev(X)
+    flags = H.HOBO_FORCE_DENSE
+    h_tc = gpuh.make(inst, flags)
+    h_cc = gpuh.make(inst, flags | H.HOBO_RESCORE_CUDA_CORES)
+    assert h_tc.info()["dense"] and h_cc.info()["dense"]
+    e_tc = h_tc.energy_fp64(Xd).cpu().numpy()
+    e_cc = h_cc.energy_fp64(Xd).cpu().numpy()
+    np.testing.assert_array_equal(e_tc, e_cc)
+    if integer:
+        np.testing.assert_array_equal(e_tc, O.energy_int(inst, X).astype(np.float64))
+    else:
+        rows = np.arange(0, B, max(1, B // 64))
+        np.testing.assert_allclose(e_tc[rows], O.energy(inst, X[rows]), rtol=1e-12, atol=1e-9)
+    h_tc.check()
+    h_tc.close()
+    h_cc.close()
+
+
+def test_dense_rescore_above_tensor_core_size():
+    """Dense layout with N > 256 (no tensor-core planes): the CUDA-core
+    exact re-score against the oracle's int64 energies."""
+    import paper_2407_19987_gb300 as H
+    inst = W.random_sparse(80, 300, 3, 0.3, "int")
+    h = gpuh.make(inst, H.HOBO_FORCE_DENSE)
+    assert h.info()["dense"]
+    X = W.random_states(81, 40, inst.N)
+    np.testing.assert_array_equal(h.energy_fp64(gpuh.to_dev(X)).cpu().numpy(),
+                                  O.energy_int(inst, X).astype(np.float64))
+    h.close()
