@@ -266,6 +266,10 @@ def run_ours(a):
     # ranks agree on the overall best state (lowest energy, lowest index)
     from paper_2407_19987_gb300.sharded import global_best, local_best
     bE, bidx, bk = local_best(hE.numpy(), state0)
+    # the result table of the last anneal (distinct best states by energy,
+    # with occurrence counts), timed apart from the step
+    H.aggregate(rr["bestX"], rr["bestE"])
+    table, agg_ms = _timed_ms(lambda: H.aggregate(rr["bestX"], rr["bestE"]))
     gE, gidx, _ = global_best(bE, bidx, hX.numpy()[bk], W_, device=dev if world > 1 else None)
 
     pk, pk_kind = peaks()
@@ -292,6 +296,9 @@ def run_ours(a):
                    "parallelism": f"replicas x{world} (independent states per GPU)",
                    "accepted_flips_per_step": accepts, "sweep_coef_bytes_per_step": coef_bytes,
                    "best_energy": gE, "best_state_index": gidx,
+                   "result_table": {"distinct_states": int(table["count"].numel()),
+                                    "top_count": int(table["count"][0].item()) if table["count"].numel() else 0,
+                                    "aggregate_ms": agg_ms},
                    "sweep_kernel_ms": sweep_avg},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": sweep_dram_bytes if a.mode == "tuned" else None,

@@ -385,6 +385,28 @@ typedef struct {
 int hobo_anneal_learned(hobo_h h, hobo_mlp_h m, uint64_t seed, int B, const float* beta, int sweeps,
                         uint32_t* bestX, double* bestE, const hobo_learned_opts* opts, void* stream);
 
+/* ---- result table ------------------------------------------------------ */
+
+/*
+ * hobo_aggregate -- the result table of a sampling run (Sec. V: states
+ * listed by energy with their occurrence counts): the distinct states among
+ * B packed states, sorted by energy ascending, ties by the lowest index at
+ * which the state occurs.
+ *   W      words per state (1..32), X device uint32 [B][W], E device double
+ *          [B] (equal states must carry equal energies, as hobo_anneal's
+ *          re-scored bestE do)
+ *   U      device uint32 [B][W]: row r = r-th distinct state (first K rows)
+ *   UE     device double [B]: its energy;  count device int64 [B]: how many
+ *          of the B states equal it;  first device int32 [B]: its lowest index
+ *   K      device int32 [1]: number of distinct states
+ * Asynchronous on `stream`; scratch is stream-ordered.  The energies order
+ * the table exactly as given (no tolerance): states whose energies differ in
+ * the last bit are different rows.
+ * Errors: HOBO_ERR_ARG, HOBO_ERR_CUDA.
+ */
+int hobo_aggregate(int W, const uint32_t* X, const double* E, int B, uint32_t* U, double* UE, int64_t* count,
+                   int32_t* first, int32_t* K, void* stream);
+
 /* Human-readable message of the last error on this thread ("" if none). */
 const char* hobo_last_error(void);
 

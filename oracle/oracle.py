@@ -234,3 +234,23 @@ def anneal_learned(inst, seed: int, B: int, betas: np.ndarray, w: dict | None, p
         y = np.where(recx == 0xFF, -1.0, (recx != best).astype(np.float64)).astype(np.float32)
         out.update(rec_F=recF, rec_x=recx, rec_y=y)
     return out
+
+
+def aggregate(X: np.ndarray, E: np.ndarray):
+    """Result table of a run: the distinct rows of X (uint8 [B, N]) with
+    their energy (that of the first occurrence), occurrence count and first
+    index, sorted by energy then first index.  Returns (states [K, N],
+    energy [K], count [K], first [K])."""
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    E = np.asarray(E, dtype=np.float64)
+    seen = {}
+    for b in range(X.shape[0]):
+        key = X[b].tobytes()
+        if key in seen:
+            seen[key][1] += 1
+        else:
+            seen[key] = [b, 1]
+    rows = sorted(seen.values(), key=lambda t: (E[t[0]], t[0]))
+    first = np.array([r[0] for r in rows], dtype=np.int64)
+    count = np.array([r[1] for r in rows], dtype=np.int64)
+    return X[first], E[first], count, first

@@ -100,6 +100,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     L.hobo_energy_fp64.argtypes = [P, P, I, P, P]
     L.hobo_anneal.argtypes = [P, U64, I, P, I, P, P, C.POINTER(hobo_anneal_opts), P]
     L.hobo_check.argtypes = [P, P]
+    L.hobo_aggregate.argtypes = [I, P, P, I, P, P, P, P, P, P]
+    L.hobo_aggregate.restype = I
     L.hobo_selftest_timeout.argtypes = [P, U64, P]
     L.hobo_selftest_timeout.restype = I
     L.hobo_energy_fp64_noalloc.argtypes = [P, P, I, P, P]
@@ -501,3 +503,21 @@ def anneal_learned(inst: Instance, mlp, seed: int, B: int, betas: np.ndarray, *,
     if recF is not None:
         out["rec_F"], out["rec_y"] = recF, recy
     return out
+
+
+def aggregate(X, E, stream=None) -> dict:
+    """hobo_aggregate: distinct states of X (int32 CUDA [B, W]) with energies
+    E (float64 CUDA [B]), sorted by energy then first index.  Returns CUDA
+    tensors states [K, W], energy [K], count [K], first [K]."""
+    import torch
+    B, W = X.shape
+    dev = X.device
+    U = torch.empty((max(B, 1), W), dtype=torch.int32, device=dev)
+    UE = torch.empty(max(B, 1), dtype=torch.float64, device=dev)
+    cnt = torch.empty(max(B, 1), dtype=torch.int64, device=dev)
+    first = torch.empty(max(B, 1), dtype=torch.int32, device=dev)
+    K = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(load_library().hobo_aggregate(W, _ptr(X), _ptr(E), B, _ptr(U), _ptr(UE), _ptr(cnt), _ptr(first),
+                                         _ptr(K), _stream(stream)))
+    k = int(K.item())
+    return {"states": U[:k], "energy": UE[:k], "count": cnt[:k], "first": first[:k]}

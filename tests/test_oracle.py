@@ -343,3 +343,31 @@ def test_anneal_recording_and_offset_states():
     part = O.anneal(inst, 3, 3, betas, state0=3)
     np.testing.assert_array_equal(full["bestX"][3:], part["bestX"])
     np.testing.assert_array_equal(full["rec"][-1], full["X"])
+
+
+def test_aggregate_hand_example():
+    """Result table: distinct states by energy, ties by first index, with
+    occurrence counts (the sampler output of Sec. V)."""
+    a, b, c = [1, 0, 1], [0, 1, 1], [1, 1, 0]
+    X = np.array([a, b, a, c, b, a], np.uint8)
+    E = np.array([1.0, 0.0, 1.0, 0.0, 0.0, 1.0])
+    S, UE, cnt, first = O.aggregate(X, E)
+    np.testing.assert_array_equal(S, np.array([b, c, a], np.uint8))
+    np.testing.assert_array_equal(UE, [0.0, 0.0, 1.0])
+    np.testing.assert_array_equal(cnt, [2, 1, 3])
+    np.testing.assert_array_equal(first, [1, 3, 0])
+
+
+def test_aggregate_properties():
+    rng = np.random.default_rng(5)
+    pool = rng.integers(0, 2, size=(15, 9)).astype(np.uint8)
+    pick = rng.integers(0, 15, size=400)
+    X = pool[pick]
+    E = (X.astype(np.int64) * np.arange(9)).sum(1).astype(np.float64) % 5
+    S, UE, cnt, first = O.aggregate(X, E)
+    assert cnt.sum() == 400 and len({s.tobytes() for s in S}) == len(S)
+    for s, f, k in zip(S, first, cnt):
+        rows = np.nonzero((X == s).all(1))[0]
+        assert rows[0] == f and len(rows) == k
+    keys = list(zip(UE, first))
+    assert keys == sorted(keys)
