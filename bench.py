@@ -359,7 +359,8 @@ def run_ours(a):
         line["time_to_target"] = measure_time_to_target_dense(h, B)
         line["extras"] = {"uneven_batch": measure_uneven_batch(),
                           "int_encoded": measure_int_encoded(),
-                          "learned_proposal": measure_learned()}
+                          "learned_proposal": measure_learned(),
+                          "tensor_train": measure_tt()}
     if rank == 0 and not a.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(inst, betas, a.cpu_states)
         cores = host_cores()
@@ -571,6 +572,31 @@ def measure_learned(n_train: int = 64, test_seeds=(5000, 5001, 5002, 5003)):
             "learned_opts": {k: v for k, v in learned_kw.items()},
             "per_instance": per,
             "geomean_ttt_ms": {"tuned": gm("tuned"), "learned": gm("learned"), "plain_fp32": gm("plain_fp32")}}
+
+
+def measure_tt(order: int = 3, N: int = 256, r: int = 16, B: int = 4096):
+    """Tensor-train contraction (Sec. VI) of a random train (order 3, N=256,
+    interior ranks 16) with 4096 states: time per call and the dense
+    tensor-core contraction of the same tensor (its full N^3 form, 3 bf16
+    planes) for scale."""
+    import torch
+
+    import paper_2407_19987_gb300 as H
+    from paper_2407_19987_gb300.tt import TensorTrain
+    rng = np.random.default_rng(7)
+    ranks = [1] + [r] * (order - 1) + [1]
+    cores = [(rng.standard_normal((ranks[c], N, ranks[c + 1])) / np.sqrt(N * ranks[c])).astype(np.float32)
+             for c in range(order)]
+    tt = TensorTrain(cores)
+    X = torch.from_numpy(W.pack_bits(W.random_states(8, B, N)).view(np.int32)).cuda()
+    tt.energy(X)
+    ms = statistics.mean(_timed_ms(lambda: tt.energy(X))[1] for _ in range(5))
+    set_bits = float(W.random_states(8, B, N).sum()) / B
+    flops = 2.0 * set_bits * sum(ranks[c] * ranks[c + 1] for c in range(order)) * B
+    tt.close()
+    return {"workload": f"random train order {order}, N={N}, interior ranks {r}, B={B}",
+            "ms": ms, "states_per_s": B / (ms / 1000.0), "algorithmic_flops": flops,
+            "gflops": flops / (ms / 1000.0) / 1e9}
 
 
 def run_kernel_case(a):

@@ -385,6 +385,27 @@ typedef struct {
 int hobo_anneal_learned(hobo_h h, hobo_mlp_h m, uint64_t seed, int B, const float* beta, int sweeps,
                         uint32_t* bestX, double* bestE, const hobo_learned_opts* opts, void* stream);
 
+/* ---- tensor-train contraction ----------------------------------------- */
+
+/*
+ * A tensor in tensor-train form (Sec. VI): A[i1..id] = G_1[:, i1, :] ...
+ * G_d[:, id, :] with cores G_c of shape [r_{c-1}][N][r_c], r_0 = r_d = 1 (the
+ * successive-SVD decomposition of Sec. VI; the package's tt.py computes it).
+ * hobo_tt_energy contracts the train with each state in every slot,
+ * E(x) = sum over index tuples of A[i1..id] x_i1...x_id = M_1 ... M_d,
+ * M_c = sum_i x_i G_c[:, i, :] (for a HOBO tensor: the energy of Sec. II.C),
+ * at d*N*r^2 work per state instead of N^d.  Float32 sums.
+ *   order 1..8, N 1..1024, ranks[0..order] host (interior ranks 1..256),
+ *   cores host float32, the cores concatenated, core c row-major
+ *   [r_{c-1}][N][r_c]; copied (caller keeps ownership).
+ *   X device uint32 [B][ceil(N/32)] packed states; E device float [B].
+ * Errors: HOBO_ERR_ARG, HOBO_ERR_ORDER, HOBO_ERR_OOM, HOBO_ERR_CUDA.
+ */
+typedef struct hobo_tt* hobo_tt_h;
+int hobo_tt_create(hobo_tt_h* out, int order, int N, const int* ranks, const float* cores);
+void hobo_tt_destroy(hobo_tt_h t);
+int hobo_tt_energy(hobo_tt_h t, const uint32_t* X, int B, float* E, void* stream);
+
 /* ---- result table ------------------------------------------------------ */
 
 /*

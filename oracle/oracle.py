@@ -254,3 +254,44 @@ def aggregate(X: np.ndarray, E: np.ndarray):
     first = np.array([r[0] for r in rows], dtype=np.int64)
     count = np.array([r[1] for r in rows], dtype=np.int64)
     return X[first], E[first], count, first
+
+
+def tt_svd(T: np.ndarray, rel_tol: float = 1e-10) -> list:
+    """Tensor-train decomposition by successive SVDs (Sec. VI): reshape the
+    remainder to (r_{c-1} n_c) x rest, SVD it, keep the singular values above
+    rel_tol times the largest as core c, carry Sigma V* on.  Cores
+    G_c [r_{c-1}, n_c, r_c], r_0 = r_d = 1."""
+    T = np.asarray(T, dtype=np.float64)
+    d, n = T.ndim, T.shape
+    cores, r, C = [], 1, T.reshape(1, -1)
+    for c in range(d - 1):
+        C = C.reshape(r * n[c], -1)
+        U, s, Vt = np.linalg.svd(C, full_matrices=False)
+        rk = max(1, int((s > rel_tol * s[0]).sum())) if s.size and s[0] > 0 else 1
+        cores.append(U[:, :rk].reshape(r, n[c], rk))
+        C = s[:rk, None] * Vt[:rk]
+        r = rk
+    cores.append(C.reshape(r, n[d - 1], 1))
+    return cores
+
+
+def tt_full(cores) -> np.ndarray:
+    """The tensor a train represents: A[i1..id] = G1[:, i1, :] ... Gd[:, id, :]."""
+    A = cores[0]
+    for G in cores[1:]:
+        A = np.tensordot(A, G, axes=([A.ndim - 1], [0]))
+    return A.reshape(A.shape[1:-1])
+
+
+def tt_energy(cores, X: np.ndarray) -> np.ndarray:
+    """E(x) = sum over all index tuples of A[i1..id] x_i1 ... x_id for each
+    row x of X, by contracting every core with x: the product of the
+    matrices M_c = sum_i x_i G_c[:, i, :], in float64."""
+    X = np.asarray(X, dtype=np.float64)
+    out = np.zeros(X.shape[0])
+    for b in range(X.shape[0]):
+        v = np.ones((1,))
+        for G in cores:
+            v = v @ np.einsum("i,aib->ab", X[b], np.asarray(G, dtype=np.float64))
+        out[b] = v[0]
+    return out

@@ -100,6 +100,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     L.hobo_energy_fp64.argtypes = [P, P, I, P, P]
     L.hobo_anneal.argtypes = [P, U64, I, P, I, P, P, C.POINTER(hobo_anneal_opts), P]
     L.hobo_check.argtypes = [P, P]
+    L.hobo_tt_create.argtypes = [C.POINTER(P), I, I, P, P]
+    L.hobo_tt_create.restype = I
+    L.hobo_tt_destroy.argtypes = [P]
+    L.hobo_tt_destroy.restype = None
+    L.hobo_tt_energy.argtypes = [P, P, I, P, P]
+    L.hobo_tt_energy.restype = I
     L.hobo_aggregate.argtypes = [I, P, P, I, P, P, P, P, P, P]
     L.hobo_aggregate.restype = I
     L.hobo_selftest_timeout.argtypes = [P, U64, P]

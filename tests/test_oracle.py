@@ -371,3 +371,41 @@ def test_aggregate_properties():
         assert rows[0] == f and len(rows) == k
     keys = list(zip(UE, first))
     assert keys == sorted(keys)
+
+
+def test_tt_decomposition_of_the_tsp_tensor_has_the_printed_bond_dimensions():
+    """Sec. VI.F: the order-6 (6,...,6) TSP tensor decomposes exactly into
+    cores (6,2), (2,6,3), (3,6,4), (4,6,4), (4,6,2), (2,6); the train
+    reproduces the tensor and its energies on all 64 states."""
+    inst = polyexp.tsp_intenc()
+    T = inst.dense().astype(np.float64)
+    cores = O.tt_svd(T)
+    assert [G.shape for G in cores] == [(1, 6, 2), (2, 6, 3), (3, 6, 4), (4, 6, 4), (4, 6, 2), (2, 6, 1)]
+    np.testing.assert_allclose(O.tt_full(cores), T, atol=1e-9 * np.abs(T).max())
+    X = np.array([[(s >> i) & 1 for i in range(6)] for s in range(64)], np.uint8)
+    np.testing.assert_allclose(O.tt_energy(cores, X), O.energy(inst, X), atol=1e-7)
+
+
+def test_tt_network_einsum_path_matches_report():
+    """Sec. VI.F: numpy's path for x contracted with the six cores costs 701
+    flops with a largest intermediate of 16 elements."""
+    shapes = [(6, 2), (2, 6, 3), (3, 6, 4), (4, 6, 4), (4, 6, 2), (2, 6)]
+    ops = [np.ones(6)] * 6 + [np.ones(s) for s in shapes]
+    _, info = np.einsum_path("i,j,k,l,m,n,iA,AjB,BkC,ClD,DmE,En->", *ops, optimize="greedy")
+    assert "7.010e+02" in info and "1.600e+01" in info
+
+
+def test_tt_energy_closed_forms():
+    """A rank-1 train is an outer product: E = prod_c (g_c . x); a random
+    train equals the energy of its full tensor by brute force."""
+    rng = np.random.default_rng(9)
+    gs = [rng.standard_normal(7) for _ in range(3)]
+    cores = [g.reshape(1, 7, 1) for g in gs]
+    X = rng.integers(0, 2, size=(20, 7))
+    np.testing.assert_allclose(O.tt_energy(cores, X), np.prod([X @ g for g in gs], axis=0), rtol=1e-12)
+    cores = [rng.standard_normal((1, 5, 3)), rng.standard_normal((3, 5, 2)), rng.standard_normal((2, 5, 1))]
+    A = O.tt_full(cores)
+    X = np.array([[(s >> i) & 1 for i in range(5)] for s in range(32)], np.float64)
+    want = np.einsum("ijk,bi,bj,bk->b", A, X, X, X)
+    np.testing.assert_allclose(O.tt_energy(cores, X), want, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(O.tt_full(O.tt_svd(A)), A, atol=1e-10)
