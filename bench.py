@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--mode", default="tuned", choices=["tuned", "plain"])
     ap.add_argument("--cpu-states", type=int, default=8, help="oracle sample size (states)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-case", default=None, choices=["sweep", "tc", "fix", "fields"],
+    ap.add_argument("--kernel-case", default=None, choices=["sweep", "tc", "fix", "fields", "tc4"],
                     help="run one small case of one kernel (for profilers) and exit")
     ap.add_argument("--case-states", type=int, default=4096)
     ap.add_argument("--case-sweeps", type=int, default=30)
@@ -360,7 +360,8 @@ def run_ours(a):
         line["extras"] = {"uneven_batch": measure_uneven_batch(),
                           "int_encoded": measure_int_encoded(),
                           "learned_proposal": measure_learned(),
-                          "tensor_train": measure_tt()}
+                          "tensor_train": measure_tt(),
+                          "order4_contraction": measure_tc4()}
     if rank == 0 and not a.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(inst, betas, a.cpu_states)
         cores = host_cores()
@@ -599,19 +600,46 @@ def measure_tt(order: int = 3, N: int = 256, r: int = 16, B: int = 4096):
             "gflops": flops / (ms / 1000.0) / 1e9}
 
 
+def measure_tc4(N: int = 64, B: int = 4096):
+    """Energies and fields of 4096 states for a dense order-4 instance (all
+    679 120 monomials of degree 1..4 over N=64 variables, N(0,1)): the
+    order-4 tensor-core path (quartic part on tcgen05) against the
+    term-list path of the same instance."""
+    import torch
+
+    import paper_2407_19987_gb300 as H
+    inst = W.dense_all_degrees(64, N, 4, "normal")
+    h = H.Instance.from_terms(inst.idx, inst.coef, inst.N)
+    X = torch.from_numpy(W.pack_bits(W.random_states(9, B, N)).view(np.int32)).cuda()
+    out = {"workload": f"dense order 4, N={N}, every monomial of degree 1..4 ({inst.nnz} terms) N(0,1), B={B}"}
+    for name, path in (("tensor_core", H.PATH_TENSOR_CORE), ("term_list", H.PATH_TERMS)):
+        h.energy(X, path=path)
+        out[name + "_ms"] = statistics.mean(_timed_ms(lambda: h.energy(X, path=path))[1] for _ in range(5))
+    # quartic part issued on the tensor cores: 3 planes x B x N x (N4*64 rows) x 64 x 2
+    n4 = (N + 3) & ~3
+    out["tensor_core_issued_tflops"] = 3 * B * N * n4 * 64 * 64 * 2 / (out["tensor_core_ms"] / 1000.0) / 1e12
+    out["speedup"] = out["term_list_ms"] / out["tensor_core_ms"]
+    h.close()
+    return out
+
+
 def run_kernel_case(a):
     """One small case of one kernel, for profilers.  Dense workload: sweep:
     an anneal of --case-states states over --case-sweeps sweeps of the
     schedule from --case-offset; tc: two tensor-core contractions of 4096
     random states; fix: two exact re-scores of 4096 random states.  fields:
     two term-list energy+field contractions of 4096 random states of the
-    sparse order-4 workload (N=96, 2% density)."""
+    sparse order-4 workload (N=96, 2% density).  tc4: two order-4
+    tensor-core contractions of 4096 random states of a dense order-4
+    instance (N=64)."""
     import torch
 
     import paper_2407_19987_gb300 as H
     inst, betas, B, S = workload()
     if a.kernel_case == "fields":
         inst = W.sparse_order4(5000)
+    elif a.kernel_case == "tc4":
+        inst = W.dense_all_degrees(64, 64, 4, "normal")
     h = H.Instance.from_terms(inst.idx, inst.coef, inst.N)
     if a.kernel_case == "sweep":
         h.anneal(2, a.case_states, betas[a.case_offset:a.case_offset + a.case_sweeps])
@@ -619,6 +647,10 @@ def run_kernel_case(a):
         X = torch.from_numpy(W.pack_bits(W.random_states(1, 4096, inst.N)).view(np.int32)).cuda()
         for _ in range(2):
             h.energy(X, path=H.PATH_TERMS)
+    elif a.kernel_case == "tc4":
+        X = torch.from_numpy(W.pack_bits(W.random_states(1, 4096, inst.N)).view(np.int32)).cuda()
+        for _ in range(2):
+            h.energy(X, path=H.PATH_TENSOR_CORE)
     else:
         X = torch.from_numpy(W.pack_bits(W.random_states(1, 4096, inst.N)).view(np.int32)).cuda()
         for _ in range(2):

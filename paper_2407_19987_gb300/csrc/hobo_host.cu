@@ -94,7 +94,7 @@ static void free_layouts(DevLayouts& d)
 {
     void* ptrs[] = {d.tvars, d.tfix, d.fptr, d.fvars, d.ffix, d.cptr, d.chdr,
                     d.ltgt, d.lcnt, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf, d.S3limb, d.rs_a, d.rs_S2,
-                    d.C3fix, d.S2fix, d.afix, d.pair_m, d.pair_j};
+                    d.C3fix, d.S2fix, d.afix, d.pair_m, d.pair_j, d.S4bf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DevLayouts{};
@@ -177,6 +177,70 @@ static int build_exact_limbs(hobo_instance* h, const std::vector<Entry>& mono)
     if (make_tc_tensor_map_rs(h) != cudaSuccess) {
         (void)cudaGetLastError();
         d.tmap_rs_ok = false;
+    }
+    return HOBO_OK;
+}
+
+static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned flags);
+
+static void destroy_instance(hobo_instance* h)
+{
+    if (!h) return;
+    destroy_instance(h->low);
+    free_layouts(h->d);
+    if (h->status && h->owns_status) cudaFree(h->status);
+    delete h;
+}
+
+// Order-4 tensor-core layout: the quartic part as split bf16 planes of the
+// symmetric tensor (every permutation of a monomial's four indices holds
+// its coefficient), the lower degrees as a child instance on the term-list
+// path.  Left out (term-list path for everything) if the planes cannot be
+// described to TMA.
+static int build_tc4(hobo_instance* h, const std::vector<Entry>& mono, unsigned flags, double maxabs)
+{
+    DevLayouts& d = h->d;
+    const int N = h->N;
+    std::vector<Entry> lower;
+    for (auto& e : mono)
+        if (e.m.d < 4) lower.push_back(e);
+    if (!lower.empty()) {
+        hobo_instance* lo = new (std::nothrow) hobo_instance();
+        if (!lo) return fail(HOBO_ERR_OOM, "host allocation failed");
+        lo->N = N;
+        lo->order = 3;
+        lo->device = h->device;
+        lo->num_sms = h->num_sms;
+        lo->status = h->status;
+        lo->owns_status = false;
+        const int rc = build_instance(lo, lower, HOBO_FORCE_SPARSE);
+        if (rc != HOBO_OK) { destroy_instance(lo); return rc; }
+        h->low = lo;
+    }
+    int nsplit = 3;
+    if (h->integer && maxabs < 65536.0 && !(flags & HOBO_SPLIT3)) nsplit = 2;
+    if (!h->integer && (flags & HOBO_SPLIT2)) nsplit = 2;
+    const int N4 = (N + 3) & ~3;
+    d.nsplit4 = nsplit;
+    d.R4 = N4 * 64;
+    const size_t plane = (size_t)N * d.R4 * 64;
+    std::vector<uint16_t> planes(plane * nsplit, 0);
+    for (auto& e : mono) {
+        if (e.m.d != 4) continue;
+        uint16_t sp[3];
+        choose_split(e.c, nsplit, sp);
+        int v[4] = {e.m.v[0], e.m.v[1], e.m.v[2], e.m.v[3]};
+        std::sort(v, v + 4);
+        do {
+            const size_t at = ((size_t)v[0] * d.R4 + (size_t)v[1] * 64 + v[2]) * 64 + v[3];
+            for (int q = 0; q < nsplit; ++q) planes[q * plane + at] = sp[q];
+        } while (std::next_permutation(v, v + 4));
+    }
+    int rc;
+    if ((rc = upload(&d.S4bf, planes))) return rc;
+    if (make_tc4_tensor_map(h) != cudaSuccess) {
+        (void)cudaGetLastError();
+        d.tmap4_ok = false;
     }
     return HOBO_OK;
 }
@@ -350,6 +414,14 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
             if (!(flags & HOBO_RESCORE_CUDA_CORES) && (rc = build_exact_limbs(h, mono))) return rc;
         }
     } else {
+        // order-4 tensor-core contraction when the quartic part is dense
+        if (K == 4 && N <= 64 && !(flags & HOBO_FORCE_SPARSE)) {
+            const double c4 = (double)N * (N - 1) * (N - 2) * (N - 3) / 24.0;
+            if ((flags & HOBO_FORCE_DENSE) || (c4 > 0 && (double)h->terms[4] >= 0.25 * c4)) {
+                const int rc4 = build_tc4(h, mono, flags, maxabs);
+                if (rc4 != HOBO_OK) return rc4;
+            }
+        }
         // (3) update lists grouped by (flipped bit i, target j)
         const int KU = h->KU;
         std::vector<int32_t> cnt((size_t)N * N, 0);
@@ -480,9 +552,7 @@ static int create_from_entries(hobo_h* out, std::vector<Entry>& ent, int order, 
     const int rc = build_instance(h, mono, flags);
     if (rc != HOBO_OK) {
         const std::string msg = g_err;
-        free_layouts(h->d);
-        cudaFree(h->status);
-        delete h;
+        destroy_instance(h);
         set_error(msg);
         return rc;
     }
@@ -505,11 +575,17 @@ using namespace hobo;
 int hobo::energy_dispatch(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g, bool flip,
                           int path, cudaStream_t st)
 {
+    if ((path == 2 || path == 0) && tc4_supported(h)) {
+        cudaError_t e = launch_energy_tc4(h, X, B, E, g, flip, st);
+        if (e == cudaSuccess) return HOBO_OK;
+        return cuda_fail(e, "order-4 tensor-core contraction");
+    }
     if (path == 2 || (path == 0 && h->dense)) {
         cudaError_t e = launch_energy_tc(h, X, B, E, g, flip, st);
         if (e == cudaSuccess) return HOBO_OK;
         if (e != cudaErrorNotSupported) return cuda_fail(e, "tensor-core contraction");
-        if (path == 2) return fail(HOBO_ERR_UNSUPPORTED, "tensor-core path needs a dense order-3 instance");
+        if (path == 2)
+            return fail(HOBO_ERR_UNSUPPORTED, "tensor-core path needs a dense order-3 or order-4 instance");
         (void)cudaGetLastError();
     }
     cudaError_t e = launch_energy_terms(h, X, B, E, g, flip, st);
@@ -576,10 +652,7 @@ int hobo_create_terms(hobo_h* out, const int32_t* idx, const float* coef, int64_
 
 void hobo_destroy(hobo_h h)
 {
-    if (!h) return;
-    free_layouts(h->d);
-    if (h->status) cudaFree(h->status);
-    delete h;
+    destroy_instance(h);
 }
 
 int hobo_check(hobo_h h, void* stream)

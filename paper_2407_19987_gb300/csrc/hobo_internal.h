@@ -77,6 +77,15 @@ struct DevLayouts {
     int rs_L = 0, rs_shift = 0;
     alignas(64) unsigned char tmap_rs[128] = {};
     bool tmap_rs_ok = false;
+    // order-4 tensor-core contraction (order-4 instances, N <= 64, quartic
+    // part dense): the symmetric quartic tensor as bf16 split planes
+    // [nsplit4][N][R4][64], row (j, k) = j * 64 + k (k >= N zero), R4 = (N
+    // rounded up to 4) * 64, K = l padded to 64; monomials of degree <= 3
+    // go to a child instance on the term-list path.
+    uint16_t* S4bf = nullptr;
+    int nsplit4 = 0, R4 = 0;
+    alignas(64) unsigned char tmap4[128] = {};
+    bool tmap4_ok = false;
 };
 
 }  // namespace hobo
@@ -91,6 +100,8 @@ struct hobo_instance {
     int num_sms = 0;
     int* status = nullptr;   // device status word written by kernels that give up a wait
     hobo::DevLayouts d;
+    hobo_instance* low = nullptr;   // order-4 tensor-core instances: the degree <= 3 part
+    bool owns_status = true;
 };
 
 namespace hobo {
@@ -136,6 +147,10 @@ bool exact_tc_supported(const hobo_instance* h);
 cudaError_t launch_wait_timeout_selftest(const hobo_instance* h, uint64_t limit_ns, cudaStream_t st);
 cudaError_t make_tc_tensor_map(hobo_instance* h);
 cudaError_t make_tc_tensor_map_rs(hobo_instance* h);
+cudaError_t make_tc4_tensor_map(hobo_instance* h);
+bool tc4_supported(const hobo_instance* h);
+cudaError_t launch_energy_tc4(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g_or_dE,
+                              bool flip_out, cudaStream_t st);
 cudaError_t launch_energy_exact_tc(const hobo_instance* h, const uint32_t* X, int B, unsigned long long* acc,
                                    cudaStream_t st);
 

@@ -516,7 +516,8 @@ bool tc_supported(const hobo_instance* h)
     return h->dense && h->d.S3bf && h->d.tmap_ok && h->N <= 256;
 }
 
-static cudaError_t encode_planes_map(void* map_out, const void* base, int planes, int N, int NJ, int KP)
+static cudaError_t encode_planes_map(void* map_out, const void* base, int planes, int N, int NJ, int KP,
+                                     int box_rows)
 {
     using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -527,7 +528,7 @@ static cudaError_t encode_planes_map(void* map_out, const void* base, int planes
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
     cuuint64_t dims[2] = {(cuuint64_t)KP, (cuuint64_t)planes * N * NJ};
     cuuint64_t strides[1] = {(cuuint64_t)KP * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kTcKB, (cuuint32_t)NJ};
+    cuuint32_t box[2] = {(cuuint32_t)kTcKB, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = reinterpret_cast<EncodeFn>(fn)(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                                                 2, const_cast<void*>(base), dims, strides, box, estr,
@@ -539,7 +540,7 @@ static cudaError_t encode_planes_map(void* map_out, const void* base, int planes
 cudaError_t make_tc_tensor_map(hobo_instance* h)
 {
     const auto& d = h->d;
-    cudaError_t e = encode_planes_map(h->d.tmap, d.S3bf, d.nsplit, h->N, d.NJ, d.KP);
+    cudaError_t e = encode_planes_map(h->d.tmap, d.S3bf, d.nsplit, h->N, d.NJ, d.KP, d.NJ);
     h->d.tmap_ok = e == cudaSuccess;
     return e;
 }
@@ -547,8 +548,319 @@ cudaError_t make_tc_tensor_map(hobo_instance* h)
 cudaError_t make_tc_tensor_map_rs(hobo_instance* h)
 {
     const auto& d = h->d;
-    cudaError_t e = encode_planes_map(h->d.tmap_rs, d.S3limb, d.rs_L, h->N, d.NJ, d.KP);
+    cudaError_t e = encode_planes_map(h->d.tmap_rs, d.S3limb, d.rs_L, h->N, d.NJ, d.KP, d.NJ);
     h->d.tmap_rs_ok = e == cudaSuccess;
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// Order-4 tensor-core contraction: the symmetric quartic tensor reshaped to
+// (N^3 x N) rows (m, j, k), K = l, against the bit matrix (the next index of
+// the one-at-a-time contraction order of Sec. VI).  Items are (m, chunk of
+// 256 rows (j, k)); the epilogue adds the accumulators of rows whose bits
+// j and k are both set: c_bm = sum_{j,k,l} S4[m][j][k][l] x_j x_k x_l =
+// 6 g4_bm (the quartic part of the field), and sum_m x_bm c_bm = 24 E4.
+// Same roles, stages and bounded waits as the order-3 kernel.
+// ---------------------------------------------------------------------------
+struct Tc4Params {
+    const uint32_t* X;
+    int B, N, W, R4, nsplit;
+    int T, chunks, G;
+    float* G4;        // [B][N] quartic field parts
+    float* Epart;     // [G][128][4]
+    int* status;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+energy_tc4_kernel(const __grid_constant__ CUtensorMap tmap, const Tc4Params p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr int NJ4 = 256;
+    const uint32_t stage_bytes = (uint32_t)NJ4 * 128u;
+    uint8_t* sA = smem;                          // one K block (l < 64)
+    uint8_t* sB = sA + 16384;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kTcStages * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kTcStages;
+    uint64_t* afull = bars + 2 * kTcStages;
+    uint64_t* aempty = afull + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(aempty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+    volatile int* never_set = abort_flag + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = p.N, W = p.W, B = p.B;
+    const int nch4 = p.R4 / NJ4;                 // row chunks per m
+    const int c = blockIdx.x;
+    const int tile_c = c % p.T, chunk = c / p.T;
+    const int i0 = tile_c * N + (int)((int64_t)chunk * N / p.chunks);
+    const int i1 = tile_c * N + (int)((int64_t)(chunk + 1) * N / p.chunks);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&afull[s], 1);
+            mbar_init(&aempty[s], 4);
+        }
+        *abort_flag = 0;
+        *never_set = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    int pstage = 0;
+    uint32_t pphase = 0;
+    uint32_t armed_phase[kTcStages];
+    bool armed[kTcStages];
+    for (int s = 0; s < kTcStages; ++s) { armed[s] = false; armed_phase[s] = 0; }
+    int cstage = 0;
+    uint32_t cphase = 0;
+    int acc_mma = 0, acc_epi = 0;
+    const uint32_t idesc = idesc_bf16(kTcM, NJ4);
+
+    int seg = 0;
+    for (int it = i0; it < i1; ++seg) {
+        const int tile = it / N;
+        const int seg_end = min(i1, (tile + 1) * N);
+        // A operand: bits l < 64 of the tile's 128 states, bf16, swizzled
+        for (int q = threadIdx.x; q < kTcM * 8; q += blockDim.x) {
+            const int r = q >> 3, ch = q & 7;
+            const int b = tile * kTcM + r;
+            const int l0 = ch * 8;
+            uint32_t byte = 0;
+            if (b < B && l0 < N) {
+                byte = (p.X[(int64_t)b * W + (l0 >> 5)] >> (l0 & 31)) & 0xFFu;
+                const int rem = N - l0;
+                if (rem < 8) byte &= (1u << rem) - 1u;
+            }
+            uint32_t wv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t lo = ((byte >> (2 * e)) & 1u) ? 0x3F80u : 0u;
+                const uint32_t hi = ((byte >> (2 * e + 1)) & 1u) ? 0x3F80u : 0u;
+                wv[e] = lo | (hi << 16);
+            }
+            uint8_t* dst = sA + (r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4);
+            *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+
+        if (warp == 0) {
+            if (lane == 0) {
+                for (int j = it; j < seg_end && !*abort_flag; ++j) {
+                    const int m = j % N;
+                    for (int cc = 0; cc < nch4; ++cc)
+                        for (int q = 0; q < p.nsplit; ++q) {
+                            if (!mbar_wait(&empty[pstage], pphase ^ 1u, abort_flag)) {
+                                set_abort(abort_flag, p.status);
+                                break;
+                            }
+                            mbar_expect_tx(&full[pstage], stage_bytes);
+                            tma_load_2d(sB + pstage * stage_bytes, &tmap, 0, (q * N + m) * p.R4 + cc * NJ4,
+                                        &full[pstage]);
+                            armed[pstage] = true;
+                            armed_phase[pstage] = pphase;
+                            if (++pstage == kTcStages) { pstage = 0; pphase ^= 1u; }
+                        }
+                }
+            }
+        } else if (warp == 1) {
+            if (lane == 0) {
+                bool ok = true;
+                for (int j = it; j < seg_end && ok && !*abort_flag; ++j) {
+                    for (int cc = 0; cc < nch4 && ok; ++cc) {
+                        const int buf = acc_mma & 1;
+                        if (!mbar_wait(&aempty[buf], (((uint32_t)acc_mma >> 1) & 1u) ^ 1u, abort_flag)) {
+                            set_abort(abort_flag, p.status);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d = tmem + (uint32_t)(buf * 256);
+                        uint32_t accum = 0;
+                        for (int q = 0; q < p.nsplit; ++q) {
+                            if (!mbar_wait(&full[cstage], cphase, abort_flag)) {
+                                set_abort(abort_flag, p.status);
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t a0 = smem_u32(sA);
+                            const uint32_t b0 = smem_u32(sB + cstage * stage_bytes);
+#pragma unroll
+                            for (int k = 0; k < kTcKB / 16; ++k) {
+                                tc_mma(d, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), idesc, accum);
+                                accum = 1;
+                            }
+                            tc_commit(&empty[cstage]);
+                            if (++cstage == kTcStages) { cstage = 0; cphase ^= 1u; }
+                        }
+                        if (!ok) break;
+                        tc_commit(&afull[buf]);
+                        ++acc_mma;
+                    }
+                }
+            }
+        } else {
+            const int quad = warp & 3;
+            const int r = quad * 32 + lane;
+            const int b = tile * kTcM + r;
+            uint32_t x[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                uint32_t v = (b < B && k < W) ? p.X[(int64_t)b * W + k] : 0u;
+                const int rem = N - 32 * k;
+                if (rem <= 0) v = 0u; else if (rem < 32) v &= (1u << rem) - 1u;
+                x[k] = v;
+            }
+            float e4 = 0.f;
+            bool ok = true;
+            for (int j = it; j < seg_end && ok; ++j) {
+                const int m = j % N;
+                float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+                for (int cc = 0; cc < nch4; ++cc) {
+                    const int buf = acc_epi & 1;
+                    ok = __all_sync(0xffffffffu, mbar_wait(&afull[buf], ((uint32_t)acc_epi >> 1) & 1u, abort_flag));
+                    if (!ok) {
+                        if (lane == 0) set_abort(abort_flag, p.status);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256);
+#pragma unroll 1
+                    for (int g = 0; g < 8; ++g) {
+                        // columns 32g..32g+31 of chunk cc: row = cc*256 + 32g + t,
+                        // j = row / 64 (fixed in the group), k = (g & 1) * 32 + t
+                        const int jj = (cc * NJ4 + 32 * g) >> 6;
+                        const uint32_t xj = jj < 32 ? (x[0] >> jj) & 1u : (x[1] >> (jj - 32)) & 1u;
+                        const uint32_t xw = xj ? x[g & 1] : 0u;
+                        if (!__any_sync(0xffffffffu, xw != 0u)) continue;
+                        uint32_t v[32];
+                        tmem_ld32(tbase + (uint32_t)(g * 32), v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int t = 0; t < 32; t += 4) {
+                            if ((xw >> t) & 1u) c0 = __fadd_rn(c0, __uint_as_float(v[t]));
+                            if ((xw >> (t + 1)) & 1u) c1 = __fadd_rn(c1, __uint_as_float(v[t + 1]));
+                            if ((xw >> (t + 2)) & 1u) c2 = __fadd_rn(c2, __uint_as_float(v[t + 2]));
+                            if ((xw >> (t + 3)) & 1u) c3 = __fadd_rn(c3, __uint_as_float(v[t + 3]));
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&aempty[buf]);
+                    ++acc_epi;
+                }
+                if (!ok) break;
+                const float cm = __fadd_rn(__fadd_rn(c0, c1), __fadd_rn(c2, c3));
+                const bool xm = ((m < 32 ? x[0] >> m : x[1] >> (m - 32)) & 1u) != 0u;
+                if (xm) e4 = __fadd_rn(e4, cm);
+                if (b < B) p.G4[(int64_t)b * N + m] = __fdiv_rn(cm, 6.0f);
+            }
+            float* dst = p.Epart + (((int64_t)c) * kTcM + r) * 4;
+            dst[0] = e4; dst[1] = 0.f; dst[2] = 0.f; dst[3] = 0.f;
+        }
+        __syncthreads();
+        it = seg_end;
+    }
+
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        for (int s = 0; s < kTcStages; ++s)
+            if (armed[s]) (void)mbar_wait(&full[s], armed_phase[s], never_set);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// E = E_low + (1/24) sum of the quartic partials of the tile's m-chunks (in
+// chunk order); g = g_low + g4 (g_low already in g when there is a lower
+// part), with dE = (1 - 2 x) g when flip.
+__global__ void energy_tc4_finalize(const float* __restrict__ Epart, const float* __restrict__ G4,
+                                    const uint32_t* __restrict__ X, int B, int N, int W, int T, int chunks,
+                                    int has_low, int flip, float* __restrict__ E, float* __restrict__ g)
+{
+    const int b = blockIdx.x;
+    if (b >= B) return;
+    const int t = b / kTcM, r = b % kTcM;
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int k = 0; k < chunks; ++k) s = __fadd_rn(s, Epart[((int64_t)(k * T + t) * kTcM + r) * 4]);
+        const float e4 = __fdiv_rn(s, 24.0f);
+        E[b] = has_low ? __fadd_rn(E[b], e4) : e4;
+    }
+    if (g) {
+        for (int m = threadIdx.x; m < N; m += blockDim.x) {
+            const int64_t at = (int64_t)b * N + m;
+            float v = has_low ? __fadd_rn(g[at], G4[at]) : G4[at];
+            if (flip && ((X[(int64_t)b * W + (m >> 5)] >> (m & 31)) & 1u)) v = -v;
+            g[at] = v;
+        }
+    }
+}
+
+bool tc4_supported(const hobo_instance* h)
+{
+    return h->order == 4 && h->d.S4bf && h->d.tmap4_ok && h->N <= 64;
+}
+
+cudaError_t make_tc4_tensor_map(hobo_instance* h)
+{
+    const auto& d = h->d;
+    cudaError_t e = encode_planes_map(h->d.tmap4, d.S4bf, d.nsplit4, h->N, d.R4, 64, 256);
+    h->d.tmap4_ok = e == cudaSuccess;
+    return e;
+}
+
+cudaError_t launch_energy_tc4(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g_or_dE,
+                              bool flip_out, cudaStream_t st)
+{
+    if (!tc4_supported(h)) return cudaErrorNotSupported;
+    if (B == 0) return cudaSuccess;
+    const auto& d = h->d;
+    cudaError_t e = cudaSuccess;
+    if (h->low) e = launch_energy_terms(h->low, X, B, E, g_or_dE, false, st);
+    if (e != cudaSuccess) return e;
+    const int tiles = (B + kTcM - 1) / kTcM;
+    const int chunks = std::max(1, std::min(h->N, h->num_sms / tiles));
+    Tc4Params p{};
+    p.X = X; p.B = B; p.N = h->N; p.W = h->W; p.R4 = d.R4; p.nsplit = d.nsplit4;
+    p.T = tiles; p.chunks = chunks; p.G = tiles * chunks; p.status = h->status;
+    float *Epart = nullptr, *G4 = nullptr;
+    e = cudaMallocAsync((void**)&Epart, sizeof(float) * (size_t)p.G * kTcM * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&G4, sizeof(float) * (size_t)B * h->N, st);
+    p.Epart = Epart;
+    p.G4 = G4;
+    const size_t sm = 1024 + 16384 + (size_t)kTcStages * 256 * 128 + 256;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(energy_tc4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) {
+        const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(d.tmap4);
+        energy_tc4_kernel<<<p.G, kTcThreads, sm, st>>>(*map, p);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        energy_tc4_finalize<<<B, 64, 0, st>>>(Epart, G4, X, B, h->N, h->W, tiles, chunks, h->low ? 1 : 0,
+                                              flip_out ? 1 : 0, E, g_or_dE);
+        e = cudaGetLastError();
+    }
+    if (Epart) cudaFreeAsync(Epart, st);
+    if (G4) cudaFreeAsync(G4, st);
     return e;
 }
 

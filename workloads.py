@@ -187,6 +187,25 @@ def random_sparse(seed: int, N: int, order: int, density: float, coef: str = "no
     return Instance(N, order, idx, c, 0.0, integer, f"sparse_N{N}_k{order}_p{density}_s{seed}")
 
 
+def dense_all_degrees(seed: int, N: int, order: int, coef: str = "normal", imax: int = 3,
+                      top_only: bool = False) -> Instance:
+    """Every monomial over distinct variables of degree 1..order (or of
+    degree `order` only) with a coefficient: N(0,1) float32 or uniform in
+    [-imax, imax] without 0.  Lower degrees padded with the smallest index."""
+    import itertools
+    rng = np.random.default_rng(seed)
+    rows = []
+    for d in ([order] if top_only else range(1, order + 1)):
+        comb = np.array(list(itertools.combinations(range(N), d)), dtype=np.int32).reshape(-1, d)
+        rows.append(np.concatenate([np.repeat(comb[:, :1], order - d, axis=1), comb], axis=1))
+    idx = np.concatenate(rows, axis=0)
+    if coef == "normal":
+        c = rng.standard_normal(idx.shape[0], dtype=np.float32)
+    else:
+        c = (rng.integers(1, imax + 1, size=idx.shape[0]) * (rng.integers(0, 2, size=idx.shape[0]) * 2 - 1)).astype(np.float32)
+    return Instance(N, order, idx, c, 0.0, coef != "normal", f"dense{order}_N{N}_s{seed}")
+
+
 def uneven_batch(seed: int = 4000, count: int = 512, nmin: int = 16, nmax: int = 192,
                  density: float = 0.05) -> list:
     """``count`` order-3 instances with N ~ U[nmin, nmax] and N(0,1)
