@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--mode", default="tuned", choices=["tuned", "plain"])
     ap.add_argument("--cpu-states", type=int, default=8, help="oracle sample size (states)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-case", default=None, choices=["sweep", "tc", "fix", "fields", "tc4"],
+    ap.add_argument("--kernel-case", default=None, choices=["sweep", "tc", "fix", "fields", "tc4", "batch"],
                     help="run one small case of one kernel (for profilers) and exit")
     ap.add_argument("--case-states", type=int, default=4096)
     ap.add_argument("--case-sweeps", type=int, default=30)
@@ -413,9 +413,10 @@ def measure_uneven_batch(plain_sample: int = 8):
     sub_flips = sum(B * i.N * S for i in insts[:plain_sample])
     p_rate = sub_flips / (p_ms_sub / 1000.0)
     shape = bt.launch_shape(0)
+    acc = int(bt.anneal(seeds[:len(bt.B)], betas, mode=H.HOBO_BATCH_GRAPH, want_accepts=True)["accepts"].sum().item())
     return {"workload": "uneven_batch: 512 order-3 instances, N~U[16,192], 5% density, N(0,1), "
                         "B=1024 each, 500 sweeps, T 5->0.02",
-            "attempted_flips": flips,
+            "attempted_flips": flips, "accepted_flips": acc,
             "graph_ms": g_ms, "graph_flips_per_s": flips / (g_ms / 1000.0),
             "per_instance_tuned_ms": t_ms, "per_instance_tuned_flips_per_s": flips / (t_ms / 1000.0),
             "per_instance_plain_flips_per_s": p_rate,
@@ -631,10 +632,23 @@ def run_kernel_case(a):
     two term-list energy+field contractions of 4096 random states of the
     sparse order-4 workload (N=96, 2% density).  tc4: two order-4
     tensor-core contractions of 4096 random states of a dense order-4
-    instance (N=64)."""
+    instance (N=64).  batch: the uneven batch (512 instances, 1024 states
+    each) through the graph form over --case-sweeps sweeps spread over its
+    schedule."""
     import torch
 
     import paper_2407_19987_gb300 as H
+    if a.kernel_case == "batch":
+        insts = W.uneven_batch(4000, 512)
+        T0, T1, S, B = W.SCHEDULES["uneven_batch"]
+        bs = W.geometric_betas(T0, T1, S)
+        idx = np.linspace(0, S - 1, a.case_sweeps).round().astype(int)
+        hs = [H.Instance.from_terms(i.idx, i.coef, i.N) for i in insts]
+        bt = H.Batch(hs, [B] * len(hs))
+        bt.anneal([4000 + t for t in range(len(hs))], bs[idx], mode=H.HOBO_BATCH_GRAPH)
+        torch.cuda.synchronize()
+        print("kernel case done: batch")
+        return 0
     inst, betas, B, S = workload()
     if a.kernel_case == "fields":
         inst = W.sparse_order4(5000)

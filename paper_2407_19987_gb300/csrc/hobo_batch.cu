@@ -202,8 +202,14 @@ static const int kTuneCtasPerSm[] = {2, 4, 6, 8};
 
 static int autotune(hobo_batch* bh, const uint64_t* seeds, const float* beta, int sweeps, cudaStream_t st)
 {
+    // the probe anneals 32 sweeps whose temperatures are spread evenly over
+    // the whole schedule, so that its mix of update-heavy (hot) and
+    // attempt-heavy (cold) sweeps resembles the full run's
     const int probe = std::max(1, std::min(sweeps, 32));
-    int rc = upload_beta(bh, beta, std::max(probe, 1), st);
+    std::vector<float> pb((size_t)probe);
+    for (int k = 0; k < probe; ++k)
+        pb[k] = beta[probe > 1 ? (int)((int64_t)k * (sweeps - 1) / (probe - 1)) : 0];
+    int rc = upload_beta(bh, pb.data(), probe, st);
     if (rc) return rc;
     if ((rc = upload_descs(bh, seeds, probe, nullptr, st))) return rc;
     cudaEvent_t e0, e1;

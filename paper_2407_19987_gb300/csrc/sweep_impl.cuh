@@ -204,6 +204,65 @@ __device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __res
     return (int64_t)(c1 - c0) * (8 + 32 * 4) + entries * (4 + 2 * KU);
 }
 
+// The same update for the batch kernel, whose instances have many short
+// chunks per bit.  The chunk headers of the bit are fetched together (lane
+// q holds header q and shuffles it out), and chunks are taken two at a time
+// with their entry loads interleaved, so that a flip waits on about half as
+// many dependent round trips to L2.  A target has one record, so chunks
+// touch disjoint fields and their order does not change any sum.
+template <int KU>
+__device__ __forceinline__ float ell_entry(const SweepDev& p, const uint32_t* __restrict__ bs, int off, int k,
+                                           int lane)
+{
+    const float cv = __ldg(p.ucoef + off + 32 * k + lane);
+    uint32_t pr = 1u;
+#pragma unroll
+    for (int s = 0; s < KU; ++s) {
+        const int v = __ldg(p.uconds + ((int64_t)off + 32 * k + lane) * KU + s);
+        pr &= bs[v >> 5] >> (v & 31);
+    }
+    return (pr & 1u) ? cv : 0.0f;
+}
+
+template <int KU>
+__device__ __forceinline__ int64_t sparse_update_paired(const SweepDev& p, float* __restrict__ g,
+                                                        const uint32_t* __restrict__ bs, int i, float delta,
+                                                        int lane)
+{
+    const int c0 = p.cptr[i], c1 = p.cptr[i + 1];
+    int64_t entries = 0;
+    for (int cb = c0; cb < c1; cb += 32) {
+        const int nc = min(32, c1 - cb);
+        const int2 myhd = lane < nc ? p.chdr[cb + lane] : make_int2(0, 0);
+        for (int q = 0; q < nc; q += 2) {
+            const bool two = q + 1 < nc;
+            const int offA = __shfl_sync(0xffffffffu, myhd.x, q);
+            const int hyA = __shfl_sync(0xffffffffu, myhd.y, q);
+            const int offB = __shfl_sync(0xffffffffu, myhd.x, two ? q + 1 : q);
+            const int hyB = two ? __shfl_sync(0xffffffffu, myhd.y, q + 1) : 0;
+            const int cA = cb + q, cB = cb + q + 1;
+            const int KA = hyA >> 6, nA = hyA & 63, KB = hyB >> 6, nB = hyB & 63;
+            const int jA = p.ltgt[32 * cA + lane];
+            const int cntA = p.lcnt[32 * cA + lane];
+            const int jB = two ? p.ltgt[32 * cB + lane] : 0;
+            const int cntB = two ? p.lcnt[32 * cB + lane] : 0;
+            entries += __reduce_add_sync(0xffffffffu, (unsigned)(cntA + cntB));
+            float accA = 0.0f, accB = 0.0f;
+            const int K = max(KA, KB);
+#pragma unroll 2
+            for (int k = 0; k < K; ++k) {
+                const float a = k < cntA ? ell_entry<KU>(p, bs, offA, k, lane) : 0.0f;
+                const float b = k < cntB ? ell_entry<KU>(p, bs, offB, k, lane) : 0.0f;
+                if (k < cntA) accA = __fadd_rn(accA, a);
+                if (k < cntB) accB = __fadd_rn(accB, b);
+            }
+            if (lane < nA) g[jA] = __fadd_rn(g[jA], __fmul_rn(delta, accA));
+            if (two && lane < nB) g[jB] = __fadd_rn(g[jB], __fmul_rn(delta, accB));
+        }
+    }
+    return (int64_t)(c1 - c0) * (8 + 32 * 4) + entries * (4 + 2 * KU);
+}
+
 // Shared-memory floats one warp needs for a state of N variables: fields,
 // bits and best bits, then the dense update's list of row offsets (read 8 at
 // a time); every part a multiple of 16 bytes.
@@ -214,7 +273,7 @@ __host__ __device__ constexpr int warp_region_floats(int N, int WMAX)
 
 // The whole anneal of state b of the instance described by p, run by one
 // warp whose shared-memory region starts at g.
-template <int WMAX, bool DENSE, int KU>
+template <int WMAX, bool DENSE, int KU, bool PAIRED = false>
 __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g, int lane)
 {
     const int N = p.N, W = p.W;
@@ -298,7 +357,8 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 } else {
                     if (lane == 0) bs[w] = cw | (w == wsent ? sent : 0u);
                     __syncwarp();
-                    nbytes += sparse_update<KU>(p, g, bs, fi, delta, lane);
+                    nbytes += PAIRED ? sparse_update_paired<KU>(p, g, bs, fi, delta, lane)
+                                      : sparse_update<KU>(p, g, bs, fi, delta, lane);
                 }
                 __syncwarp();
                 t0 = f + 1;
@@ -350,7 +410,7 @@ sweep_batch_kernel(const SweepDev* __restrict__ descs, const int2* __restrict__ 
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems) break;
         const int2 it = items[item];
-        anneal_state<WMAX, DENSE, KU>(descs[it.x], it.y, region, lane);
+        anneal_state<WMAX, DENSE, KU, true>(descs[it.x], it.y, region, lane);
         __syncwarp();
     }
 }
