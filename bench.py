@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--mode", default="tuned", choices=["tuned", "plain"])
     ap.add_argument("--cpu-states", type=int, default=8, help="oracle sample size (states)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-case", default=None, choices=["sweep", "tc", "fix", "fields", "tc4", "batch"],
+    ap.add_argument("--kernel-case", default=None, choices=["sweep", "tc", "fix", "fields", "tc4", "batch", "rescore"],
                     help="run one small case of one kernel (for profilers) and exit")
     ap.add_argument("--case-states", type=int, default=4096)
     ap.add_argument("--case-sweeps", type=int, default=30)
@@ -628,7 +628,8 @@ def run_kernel_case(a):
     """One small case of one kernel, for profilers.  Dense workload: sweep:
     an anneal of --case-states states over --case-sweeps sweeps of the
     schedule from --case-offset; tc: two tensor-core contractions of 4096
-    random states; fix: two exact re-scores of 4096 random states.  fields:
+    random states; fix: two exact re-scores of 4096 random states on CUDA
+    cores; rescore: the same on the tensor cores (limb planes).  fields:
     two term-list energy+field contractions of 4096 random states of the
     sparse order-4 workload (N=96, 2% density).  tc4: two order-4
     tensor-core contractions of 4096 random states of a dense order-4
@@ -654,13 +655,18 @@ def run_kernel_case(a):
         inst = W.sparse_order4(5000)
     elif a.kernel_case == "tc4":
         inst = W.dense_all_degrees(64, 64, 4, "normal")
-    h = H.Instance.from_terms(inst.idx, inst.coef, inst.N)
+    flags = H.HOBO_RESCORE_CUDA_CORES if a.kernel_case == "fix" else 0
+    h = H.Instance.from_terms(inst.idx, inst.coef, inst.N, flags)
     if a.kernel_case == "sweep":
         h.anneal(2, a.case_states, betas[a.case_offset:a.case_offset + a.case_sweeps])
     elif a.kernel_case == "fields":
         X = torch.from_numpy(W.pack_bits(W.random_states(1, 4096, inst.N)).view(np.int32)).cuda()
         for _ in range(2):
             h.energy(X, path=H.PATH_TERMS)
+    elif a.kernel_case == "rescore":
+        X = torch.from_numpy(W.pack_bits(W.random_states(1, 4096, inst.N)).view(np.int32)).cuda()
+        for _ in range(2):
+            h.energy_fp64(X)
     elif a.kernel_case == "tc4":
         X = torch.from_numpy(W.pack_bits(W.random_states(1, 4096, inst.N)).view(np.int32)).cuda()
         for _ in range(2):

@@ -23,6 +23,7 @@
 // of the variables m; tiles advance through m in step.  Every wait on an mbarrier gives up
 // after kWaitNs and reports HOBO_ERR_TIMEOUT through the status word.
 #include <algorithm>
+#include <vector>
 #include <cuda.h>
 #include "hobo_internal.h"
 #include "hobo_dev.cuh"
@@ -877,12 +878,15 @@ cudaError_t launch_energy_tc4(const hobo_instance* h, const uint32_t* X, int B, 
 // accumulator columns that hold only zeros (l <= m + 1, j <= m) are
 // skipped; items with no K block left are skipped by all three roles.
 // ---------------------------------------------------------------------------
+constexpr int kMaxChunks = 256;
+
 struct TcExactParams {
     const uint32_t* X;
     int B, N, W, NJ, KP, L;
     int T, chunks, G;
     unsigned long long* acc;
     int* status;
+    int mb[kMaxChunks + 1];   // m-chunk c is [mb[c], mb[c+1]), balanced by work
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -906,8 +910,8 @@ energy_tc_exact_kernel(const __grid_constant__ CUtensorMap tmap, const TcExactPa
     const int N = p.N, W = p.W, B = p.B;
     const int c = blockIdx.x;
     const int tile_c = c % p.T, chunk = c / p.T;
-    const int i0 = tile_c * N + (int)((int64_t)chunk * N / p.chunks);
-    const int i1 = tile_c * N + (int)((int64_t)(chunk + 1) * N / p.chunks);
+    const int i0 = tile_c * N + p.mb[chunk];
+    const int i1 = tile_c * N + p.mb[chunk + 1];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcStages; ++s) {
@@ -1176,10 +1180,25 @@ cudaError_t launch_energy_exact_tc(const hobo_instance* h, const uint32_t* X, in
         if (e != cudaSuccess) return e;
     }
     const int tiles = (B + kTcM - 1) / kTcM;
-    const int chunks = std::max(1, std::min(h->N, h->num_sms / tiles));
+    const int chunks = std::max(1, std::min(std::min(h->N, kMaxChunks), h->num_sms / tiles));
     TcExactParams p{};
     p.X = X; p.B = B; p.N = h->N; p.W = h->W; p.NJ = d.NJ; p.KP = d.KP; p.L = d.rs_L;
     p.T = tiles; p.chunks = chunks; p.G = tiles * chunks; p.acc = acc; p.status = h->status;
+    {
+        // m-chunk boundaries at equal shares of the work: item m has
+        // nKB - (m+2)/64 K blocks (none for the last m) plus its epilogue
+        const int nKB = d.KP / kTcKB;
+        std::vector<double> cum((size_t)h->N + 1, 0.0);
+        for (int m = 0; m < h->N; ++m) cum[m + 1] = cum[m] + std::max(0, nKB - (m + 2) / kTcKB) + 0.25;
+        p.mb[0] = 0;
+        int m = 0;
+        for (int k = 1; k < chunks; ++k) {
+            const double want = cum[h->N] * k / chunks;
+            while (m < h->N && cum[m + 1] <= want) ++m;
+            p.mb[k] = std::max(p.mb[k - 1], m);
+        }
+        p.mb[chunks] = h->N;
+    }
     const size_t sm = tc_smem_bytes(d.NJ, d.KP);
     cudaError_t e = cudaFuncSetAttribute(energy_tc_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
