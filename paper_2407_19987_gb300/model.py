@@ -192,6 +192,10 @@ class Model:
             y = y + w * x
         return y
 
+    def bits(self, name: str) -> list:
+        """The binary variables of a declared integer, in encoding order."""
+        return [Poly({(i,): 1}) for i in self.integers[name][0]]
+
     def compile(self, H, exact: bool = True) -> Compiled:
         H = Poly.lift(H)
         mons = [(k, v) for k, v in H.t.items() if k]

@@ -24,10 +24,9 @@ def pythagorean():
     x, y, z = ints
     H = (x * x + y * y - z * z) ** 2
     for n in ("x", "y", "z"):
-        ids = m.integers[n][0]
         zero = 1
-        for i in ids:
-            zero = zero * (1 - _var(i))
+        for b in m.bits(n):
+            zero = zero * (1 - b)
         H = H + 10 * zero
     return m, m.compile(H)
 
@@ -39,7 +38,3 @@ def tsp():
     xB, xC, xD = (m.integer(n, 2, msb_first=True) for n in ("xB", "xC", "xD"))
     return m, m.compile(10 * (xB * xC * xD - 6) ** 2)
 
-
-def _var(i):
-    from paper_2407_19987_gb300.model import Poly
-    return Poly({(i,): 1})

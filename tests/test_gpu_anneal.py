@@ -34,6 +34,8 @@ INT_CASES = [
     ("order4_N40", lambda: W.random_sparse(43, 40, 4, 0.02, "int"), 0, 33, (10.0, 0.1, 15)),
     ("order5_N24", lambda: W.random_sparse(44, 24, 5, 0.03, "int"), 0, 20, (10.0, 0.1, 15)),
     ("order6_N20", lambda: W.random_sparse(45, 20, 6, 0.02, "int"), 0, 20, (10.0, 0.1, 15)),
+    ("order7_N16", lambda: W.random_sparse(46, 16, 7, 0.03, "int"), 0, 20, (10.0, 0.1, 15)),
+    ("order8_N14", lambda: W.random_sparse(47, 14, 8, 0.05, "int"), 0, 20, (10.0, 0.1, 15)),
     ("pythagorean", polyexp.pythagorean, 0, 64, (400.0, 0.05, 60)),
     ("tsp", polyexp.tsp_intenc, 0, 64, (400.0, 0.05, 60)),
     ("int_encoded", lambda: W.int_encoded(3), 0, 48, (2000.0, 0.5, 40)),
@@ -160,6 +162,24 @@ def test_int_encoded_full_size_sampled_states():
         np.testing.assert_array_equal(gpuh.to_host_bits(r["bestX"][b:b + 1], inst.N), ref["bestX"])
         np.testing.assert_array_equal(r["bestE"][b:b + 1].cpu().numpy(), ref["bestE"])
         np.testing.assert_array_equal(r["accepts"][b:b + 1].cpu().numpy(), ref["accepts"])
+
+
+def test_sparse_order4_full_size_sampled_states():
+    """Order-4 workload (N=96, 2% density) at the size the learned-proposal
+    measurement anneals (B=4096, 500 sweeps); sampled states follow the
+    oracle bit for bit, and their re-scored energies are the oracle's."""
+    inst = W.sparse_order4(5000)
+    T0, T1, S, B = W.SCHEDULES["sparse_order4"]
+    betas = W.geometric_betas(T0, T1, S)
+    h = gpuh.make(inst)
+    r = _run(h, 11, B, betas, TUNED)
+    for b in (0, 1777, B - 1):
+        ref = O.anneal(inst, 11, 1, betas, state0=b)
+        np.testing.assert_array_equal(gpuh.to_host_bits(r["bestX"][b:b + 1], inst.N), ref["bestX"])
+        np.testing.assert_array_equal(r["bestE"][b:b + 1].cpu().numpy(), ref["bestE"])
+        np.testing.assert_array_equal(gpuh.to_host_bits(r["X"][b:b + 1], inst.N), ref["X"])
+        np.testing.assert_array_equal(r["accepts"][b:b + 1].cpu().numpy(), ref["accepts"])
+    h.close()
 
 
 def test_dense_float_full_size_best_energies():

@@ -37,6 +37,8 @@ INT_CASES = [
     ("order4_N40", lambda: W.random_sparse(34, 40, 4, 0.02, "int")),
     ("order5_N20", lambda: W.random_sparse(35, 20, 5, 0.05, "int")),
     ("order6_N16", lambda: W.random_sparse(36, 16, 6, 0.05, "int")),
+    ("order7_N14", lambda: W.random_sparse(37, 14, 7, 0.05, "int")),
+    ("order8_N13", lambda: W.random_sparse(38, 13, 8, 0.06, "int")),
     ("pythagorean", polyexp.pythagorean),
     ("tsp", polyexp.tsp_intenc),
     ("seating", polyexp.seating),
