@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--mode", default="tuned", choices=["tuned", "plain"])
     ap.add_argument("--cpu-states", type=int, default=8, help="oracle sample size (states)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-case", default=None, choices=["sweep", "tc", "fix", "fields", "tc4", "batch", "rescore"],
+    ap.add_argument("--kernel-case", default=None, choices=["sweep", "sweep-resume", "tc", "fix", "fields", "tc4", "batch", "rescore"],
                     help="run one small case of one kernel (for profilers) and exit")
     ap.add_argument("--case-states", type=int, default=4096)
     ap.add_argument("--case-sweeps", type=int, default=30)
@@ -627,7 +627,8 @@ def measure_tc4(N: int = 64, B: int = 4096):
 def run_kernel_case(a):
     """One small case of one kernel, for profilers.  Dense workload: sweep:
     an anneal of --case-states states over --case-sweeps sweeps of the
-    schedule from --case-offset; tc: two tensor-core contractions of 4096
+    schedule from --case-offset; sweep-resume: sweeps [0, --case-offset)
+    and then, resumed, --case-sweeps more (profile the second launch); tc: two tensor-core contractions of 4096
     random states; fix: two exact re-scores of 4096 random states on CUDA
     cores; rescore: the same on the tensor cores (limb planes).  fields:
     two term-list energy+field contractions of 4096 random states of the
@@ -659,6 +660,13 @@ def run_kernel_case(a):
     h = H.Instance.from_terms(inst.idx, inst.coef, inst.N, flags)
     if a.kernel_case == "sweep":
         h.anneal(2, a.case_states, betas[a.case_offset:a.case_offset + a.case_sweeps])
+    elif a.kernel_case == "sweep-resume":
+        # anneal sweeps [0, offset), then resume for --case-sweeps more: the
+        # second sweep launch is the profiled one, in the schedule's true state
+        off = a.case_offset
+        r = h.anneal(2, a.case_states, betas[:off], want_final=True, want_fields=True)
+        h.anneal(2, a.case_states, betas[off:off + a.case_sweeps], sweep0=off, resume=True, X=r["X"],
+                 bestX=r["bestX"], bestE32=r["bestE32"], E=r["E"], g=r["g"])
     elif a.kernel_case == "fields":
         X = torch.from_numpy(W.pack_bits(W.random_states(1, 4096, inst.N)).view(np.int32)).cuda()
         for _ in range(2):
