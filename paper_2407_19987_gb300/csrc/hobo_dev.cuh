@@ -64,21 +64,39 @@ __device__ __forceinline__ float exp2_fixed(float t)
     return __fmul_rn(p, __uint_as_float((uint32_t)(ni + 127) << 23));
 }
 
+// The same sequence without branches: arguments below -125 give 0 by a
+// select instead of an early return, so that the 32 lanes of a warp never
+// take different paths.
+__device__ __forceinline__ float exp2_fixed_nb(float t)
+{
+    const bool under = !(t >= -125.0f);
+    const float tc = under ? 0.0f : t;
+    const float n = floorf(__fadd_rn(tc, 0.5f));
+    const float f = __fsub_rn(tc, n);
+    float p = __uint_as_float(0x39218489u);
+    p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3AAEC3FFu));
+    p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3C1D955Bu));
+    p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3D635847u));
+    p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3E75FDF0u));
+    p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3F317218u));
+    p = __fadd_rn(__fmul_rn(p, f), 1.0f);
+    const int ni = (int)n;
+    const float r = __fmul_rn(p, __uint_as_float((uint32_t)(ni + 127) << 23));
+    return under ? 0.0f : r;
+}
+
 // Metropolis decision for a float flip delta dE at inverse temperature beta
 // with the 32-bit random word w: accept iff dE <= 0 or
-// (w >> 8) * 2^-24 < exp2(-(beta*dE) * log2 e).
+// (w >> 8) * 2^-24 < exp2(-(beta*dE) * log2 e).  Evaluated without branches
+// (every lane runs the same instructions): for dE <= 0 the argument is
+// clamped to 0 (p = 1 > u, the same decision), and no shortcut is taken.
 __device__ __forceinline__ bool metropolis(float dE, float beta, uint32_t w)
 {
-    if (dE <= 0.0f) return true;
     const float a = __fmul_rn(beta, dE);
-    const float t = -__fmul_rn(a, __uint_as_float(0x3FB8AA3Bu));   // log2(e)
-    // Shortcut with the same decision: for t < -26, exp2_fixed(t) <
-    // 1.42 * 2^(t + 1/2) < 2^-24, while a nonzero u is at least 2^-24, so
-    // the test can only pass for u == 0, where it passes iff p > 0.
-    if (t < -26.0f && (w >> 8) != 0u) return false;
-    const float p = exp2_fixed(t);
+    const float t = fminf(-__fmul_rn(a, __uint_as_float(0x3FB8AA3Bu)), 0.0f);   // log2(e)
+    const float p = exp2_fixed_nb(t);
     const float u = __fmul_rn((float)(w >> 8), 5.9604644775390625e-8f);  // 2^-24
-    return u < p;
+    return (dE <= 0.0f) | (u < p);
 }
 
 // Stream ids of the random counter (fourth counter word).
