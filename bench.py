@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--case-states", type=int, default=4096)
     ap.add_argument("--case-sweeps", type=int, default=30)
     ap.add_argument("--case-offset", type=int, default=0, help="first sweep of the schedule in the sweep case")
+    ap.add_argument("--clocks-csv", default=None, help="also write the raw clock samples of the timed region here")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-workload measurement")
     return ap.parse_args()
 
@@ -256,8 +257,7 @@ def run_ours(a):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
-    clocks_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else None
+    clocks_path = f"{a.clocks_csv}.rank{rank}" if a.clocks_csv else None
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
