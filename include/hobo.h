@@ -354,7 +354,7 @@ typedef struct {
                             (logit) is >= threshold */
     float top_frac;      /* order mode: fraction of bits attempted (0 = 1.0) */
     float threshold;     /* threshold mode: logit threshold */
-    int table_size;      /* grid points of the per-sweep score table (0 = 1024) */
+    int table_size;      /* grid points of the per-sweep score table (0 = 256) */
     float vmax;          /* clamp of beta*g in the features (0 = 32) */
     int rec_every;       /* record sweeps s with s % rec_every == 0 (0: none) */
     int rec_states;      /* ... for states b < rec_states */

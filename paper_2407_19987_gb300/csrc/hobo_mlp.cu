@@ -544,7 +544,7 @@ extern "C" int hobo_anneal_learned(hobo_h h, hobo_mlp_h m, uint64_t seed, int B,
     if (!std::isfinite(o.threshold)) return mfail(HOBO_ERR_ARG, "threshold must be finite");
     if (!(o.top_frac > 0.f)) o.top_frac = 1.f;
     if (o.top_frac > 1.f) o.top_frac = 1.f;
-    if (o.table_size == 0) o.table_size = 1024;
+    if (o.table_size == 0) o.table_size = 256;
     if (!(o.vmax > 0.f)) o.vmax = 32.f;
     if (o.table_size < 2 || o.table_size > (1 << 16)) return mfail(HOBO_ERR_ARG, "table_size must be 2..65536");
     const bool record = o.rec_every > 0 && o.rec_states > 0;
