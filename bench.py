@@ -313,7 +313,7 @@ def run_ours(a):
     # DRAM bytes (read + write) of one full-size launch of the dense sweep
     # kernel, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
     # profiles/sweep_tuned_dense_N256_B4096.md); the kernel is unchanged since.
-    sweep_dram_bytes = 135143168 + 2397184
+    sweep_dram_bytes = 139011584 + 2867968
     # L2 peak of this GPU as ncu reports it: lts__t_bytes.sum.peak_sustained
     # (18048 B/cycle) x L2 clock (2.017 GHz), same profile summary.
     l2_peak_gbs = 18048 * 2.0168e9 / 1e9
@@ -340,7 +340,7 @@ def run_ours(a):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": sweep_dram_bytes if a.mode == "tuned" else None,
                      "kernel": "sweep_tuned_kernel (dense)", "peak_kind": pk_kind,
-                     "note": "coefficient slabs (67 MB) stay in L2: DRAM traffic per launch is ~0.05% of the "
+                     "note": "coefficient slabs (67 MB) stay in L2: DRAM traffic per launch is ~0.06% of the "
                              "algorithmic bytes, so the bound that applies is the L2 one below",
                      "l2": {"achieved": achieved, "peak": l2_peak_gbs, "unit": "GB/s",
                             "frac": achieved / l2_peak_gbs,
