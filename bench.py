@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--mode", default="tuned", choices=["tuned", "plain"])
     ap.add_argument("--cpu-states", type=int, default=8, help="oracle sample size (states)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-case", default=None, choices=["sweep", "sweep-resume", "tc", "fix", "fields", "tc4", "batch", "rescore"],
+    ap.add_argument("--kernel-case", default=None, choices=["sweep", "sweep-resume", "tc", "fix", "fields", "tc4", "batch", "rescore", "mlp"],
                     help="run one small case of one kernel (for profilers) and exit")
     ap.add_argument("--case-states", type=int, default=4096)
     ap.add_argument("--case-sweeps", type=int, default=30)
@@ -560,6 +560,7 @@ def measure_learned(n_train: int = 64, test_seeds=(5000, 5001, 5002, 5003)):
                 res[f"{name}_S{Sx}"] = {"ms": ms, "mean_best": float(E.mean()), "hit_frac": float((E <= target).mean())}
         per.append(res)
         h.close()
+    network = measure_network_pass(net)
     net.close()
 
     def gm(key):
@@ -573,7 +574,45 @@ def measure_learned(n_train: int = 64, test_seeds=(5000, 5001, 5002, 5003)):
                          "loss_after": loss1},
             "learned_opts": {k: v for k, v in learned_kw.items()},
             "per_instance": per,
-            "geomean_ttt_ms": {"tuned": gm("tuned"), "learned": gm("learned"), "plain_fp32": gm("plain_fp32")}}
+            "geomean_ttt_ms": {"tuned": gm("tuned"), "learned": gm("learned"), "plain_fp32": gm("plain_fp32")},
+            "network_pass": network}
+
+
+def measure_network_pass(net, S: int = 500, G: int = 256, n_rows: int = 1 << 20, reps: int = 5):
+    """The proposal network's forward pass on the tensor cores (tcgen05,
+    two-plane bf16 activations) against the float32 CUDA-core passes: the
+    score tables of an S-sweep learned anneal (S x 2 x G rows) and a forward
+    pass over n_rows feature rows.  Median of `reps` CUDA-event timings."""
+    import torch
+    import workloads as W
+    Hh = net.hidden
+    betas = torch.from_numpy(W.geometric_betas(8.0, 0.05, S)).cuda()
+    rng = np.random.default_rng(2)
+    F = np.stack([np.clip(rng.standard_normal(n_rows) * 2, -4, 4), rng.integers(0, 2, n_rows) * 2.0 - 1,
+                  rng.uniform(-1.0, 0.6, n_rows)], 1).astype(np.float32)
+    Fd = torch.from_numpy(F).cuda()
+
+    def med(fn):
+        fn()
+        return float(np.median([_timed_ms(fn)[1] for _ in range(reps)]))
+
+    out = {"hidden": Hh}
+    pk, _ = peaks()
+    for name, rows, fn in (("score_tables", S * 2 * G, lambda: net.score_tables(betas, G)),
+                           ("forward", n_rows, lambda: net.forward(Fd))):
+        net.set_tensor_cores(True)
+        t_tc = med(fn)
+        net.set_tensor_cores(False)
+        t_cc = med(fn)
+        net.set_tensor_cores(True)
+        alg = 2.0 * (3 * Hh + Hh * Hh + Hh) * rows            # multiply-adds of the three layers
+        issued = 2.0 * 2 * Hh * Hh * (-(-rows // 128) * 128)  # two bf16 planes of the H x H layer
+        out[name] = {"rows": rows, "tensor_core_ms": t_tc, "cuda_core_ms": t_cc, "speedup": t_cc / t_tc,
+                     "algorithmic_tflops": alg / (t_tc / 1e3) / 1e12,
+                     "issued_tensor_tflops": issued / (t_tc / 1e3) / 1e12,
+                     "issued_frac_of_bf16_peak": issued / (t_tc / 1e3) / 1e12 / pk["bf16_tflops"]}
+    net.check()
+    return out
 
 
 def measure_tt(order: int = 3, N: int = 256, r: int = 16, B: int = 4096):
@@ -636,10 +675,24 @@ def run_kernel_case(a):
     tensor-core contractions of 4096 random states of a dense order-4
     instance (N=64).  batch: the uneven batch (512 instances, 1024 states
     each) through the graph form over --case-sweeps sweeps spread over its
-    schedule."""
+    schedule.  mlp: two tensor-core forward passes of the proposal network
+    (H=256) over --case-states x 256 feature rows."""
     import torch
 
     import paper_2407_19987_gb300 as H
+    if a.kernel_case == "mlp":
+        n = a.case_states * 256
+        rng = np.random.default_rng(2)
+        F = np.stack([np.clip(rng.standard_normal(n) * 2, -4, 4), rng.integers(0, 2, n) * 2.0 - 1,
+                      rng.uniform(-1.0, 0.6, n)], 1).astype(np.float32)
+        net = H.MLP(256, seed=1)
+        Fd = torch.from_numpy(F).cuda()
+        for _ in range(2):
+            net.forward(Fd)
+        net.check()
+        net.close()
+        print("kernel case done: mlp")
+        return 0
     if a.kernel_case == "batch":
         insts = W.uneven_batch(4000, 512)
         T0, T1, S, B = W.SCHEDULES["uneven_batch"]

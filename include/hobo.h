@@ -327,8 +327,29 @@ int64_t hobo_mlp_num_params(hobo_mlp_h m);
 int hobo_mlp_get(hobo_mlp_h m, float* host, int rounded);
 /* Set the parameters from host float32 values (also resets Adam). */
 int hobo_mlp_set(hobo_mlp_h m, const float* host);
-/* Logits of n feature rows F (device [n][3]) into logit (device [n]). */
+/* Logits of n feature rows F (device [n][3]) into logit (device [n]).
+ * Networks of hidden width 64..256 (a multiple of 64) run the H x H layer
+ * on the tensor cores (tcgen05: hidden activations split into two bf16
+ * planes hi + lo, relative residual <= 2^-17, against the bf16 weights,
+ * float32 accumulation), with layer 1 and the head fused around it; other
+ * widths run float32 CUDA-core passes.  The score tables of
+ * hobo_anneal_learned use the same pass.  Errors: HOBO_ERR_ARG,
+ * HOBO_ERR_CUDA; a device-side wait that gave up shows at hobo_mlp_check. */
 int hobo_mlp_forward(hobo_mlp_h m, const float* F, int64_t n, float* logit, void* stream);
+/* Score tables of the learned sweep: tables (device [S][2][G]) gets, for
+ * sweep s (beta device [S]), bit value x and point k, the logit of the
+ * features (v_k / 8, 2x - 1, -ln(beta_s) / 4), v_k = -vmax + 2 vmax k /
+ * (G - 1) -- the table hobo_anneal_learned builds and interpolates.
+ * Errors: HOBO_ERR_ARG (G outside 2..65536, vmax <= 0, NULL pointers),
+ * HOBO_ERR_CUDA. */
+int hobo_mlp_score_tables(hobo_mlp_h m, const float* beta, int S, int G, float vmax, float* tables, void* stream);
+/* Choose the forward/table path: on = 1 tensor cores (the default where the
+ * width allows it; HOBO_ERR_UNSUPPORTED otherwise), 0 CUDA-core passes.
+ * Training passes always run on CUDA cores. */
+int hobo_mlp_set_tensor_cores(hobo_mlp_h m, int on);
+/* Wait for `stream` and report whether a network kernel gave up a bounded
+ * device-side wait since the last check (HOBO_ERR_TIMEOUT; cleared). */
+int hobo_mlp_check(hobo_mlp_h m, void* stream);
 /* Mean binary cross-entropy of rows F against labels y (device [n], 0/1)
  * and its gradient w.r.t. the bf16-rounded parameters: grad device
  * [num_params] or NULL, loss device [1] or NULL. */

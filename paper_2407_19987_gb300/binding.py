@@ -128,12 +128,16 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     L.hobo_mlp_get.argtypes = [P, P, I]
     L.hobo_mlp_set.argtypes = [P, P]
     L.hobo_mlp_forward.argtypes = [P, P, I64, P, P]
+    L.hobo_mlp_set_tensor_cores.argtypes = [P, I]
+    L.hobo_mlp_check.argtypes = [P, P]
+    L.hobo_mlp_score_tables.argtypes = [P, P, I, I, C.c_float, P, P]
     L.hobo_mlp_loss_grad.argtypes = [P, P, P, I64, P, P, P]
     L.hobo_mlp_train_step.argtypes = [P, P, P, I64, C.c_float, P, P]
     L.hobo_mlp_save.argtypes = [P, C.c_char_p]
     L.hobo_mlp_load.argtypes = [C.POINTER(P), C.c_char_p]
     L.hobo_anneal_learned.argtypes = [P, P, U64, I, P, I, P, P, C.POINTER(hobo_learned_opts), P]
-    for name in ("hobo_mlp_create", "hobo_mlp_get", "hobo_mlp_set", "hobo_mlp_forward", "hobo_mlp_loss_grad",
+    for name in ("hobo_mlp_create", "hobo_mlp_get", "hobo_mlp_set", "hobo_mlp_forward", "hobo_mlp_set_tensor_cores",
+                 "hobo_mlp_check", "hobo_mlp_score_tables", "hobo_mlp_loss_grad",
                  "hobo_mlp_train_step", "hobo_mlp_save", "hobo_mlp_load", "hobo_anneal_learned"):
         getattr(L, name).restype = I
     L.hobo_last_error.restype = C.c_char_p
@@ -446,6 +450,25 @@ class MLP:
             n = int(np.prod(shape))
             out[k] = np.asarray(flat[o:o + n], dtype=np.float64).reshape(shape)
             o += n
+        return out
+
+    def set_tensor_cores(self, on: bool):
+        """Forward passes and score tables on the tensor cores (default for
+        hidden widths 64..256, multiples of 64) or on CUDA cores."""
+        _check(load_library().hobo_mlp_set_tensor_cores(self._h, 1 if on else 0))
+
+    def check(self, stream=None):
+        """Raise HoboError if a network kernel gave up a bounded wait."""
+        _check(load_library().hobo_mlp_check(self._h, _stream(stream)))
+
+    def score_tables(self, beta, G: int = 256, vmax: float = 32.0, stream=None):
+        """The learned sweep's score tables [S, 2, G] for the device betas
+        [S] (hobo_mlp_score_tables)."""
+        import torch
+        beta = beta.contiguous()
+        out = torch.empty((beta.shape[0], 2, G), dtype=torch.float32, device=beta.device)
+        _check(load_library().hobo_mlp_score_tables(self._h, _ptr(beta), beta.shape[0], G, C.c_float(vmax),
+                                                    _ptr(out), _stream(stream)))
         return out
 
     def forward(self, F, stream=None):

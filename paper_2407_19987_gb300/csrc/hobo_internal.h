@@ -154,6 +154,15 @@ cudaError_t launch_energy_tc4(const hobo_instance* h, const uint32_t* X, int B, 
 cudaError_t launch_energy_exact_tc(const hobo_instance* h, const uint32_t* X, int B, unsigned long long* acc,
                                    cudaStream_t st);
 
+// Forward pass of the proposal network on the tensor cores (hidden width
+// 64..256, a multiple of 64): logits of the rows of F [n][3], or, with F
+// null, of the score-table rows (sweep s, bit value x, point k) of beta [S]
+// with G points over [-vmax, vmax].  Returns cudaErrorNotSupported for other
+// widths.
+bool mlp_tc_supported(int H);
+cudaError_t launch_mlp_forward_tc(const float* w, int H, int64_t n, const float* F, const float* beta, int G,
+                                  float vmax, float* out, int* status, cudaStream_t st);
+
 void set_error(const std::string& msg);
 
 // Energy/field contraction with the automatic or explicit path (0 auto,

@@ -35,6 +35,8 @@ struct hobo_mlp {
     // activations of a training pass, grown on demand
     float* act = nullptr;
     int64_t act_rows = 0;
+    int* status = nullptr;     // device word: a bounded wait of a network kernel gave up
+    bool use_tc = false;       // forward passes and score tables on the tensor cores
 };
 
 namespace hobo {
@@ -316,6 +318,7 @@ int hobo_mlp_create(hobo_mlp_h* out, int hidden, uint64_t seed)
     hobo_mlp* m = new (std::nothrow) hobo_mlp();
     if (!m) return mfail(HOBO_ERR_OOM, "host allocation");
     m->H = hidden;
+    m->use_tc = mlp_tc_supported(hidden);
     cudaGetDevice(&m->device);
     const MlpOff o = offsets(hidden);
     m->nparam = o.n;
@@ -330,6 +333,8 @@ int hobo_mlp_create(hobo_mlp_h* out, int hidden, uint64_t seed)
     if (e == cudaSuccess) e = cudaMalloc((void**)&m->m1, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&m->m2, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&m->grad, bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(m->master, w.data(), bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->m1, 0, bytes);
     if (e == cudaSuccess) e = cudaMemset(m->m2, 0, bytes);
@@ -349,13 +354,37 @@ int hobo_mlp_create(hobo_mlp_h* out, int hidden, uint64_t seed)
 void hobo_mlp_destroy(hobo_mlp_h m)
 {
     if (!m) return;
-    void* ptrs[] = {m->master, m->bf, m->m1, m->m2, m->grad, m->act};
+    void* ptrs[] = {m->master, m->bf, m->m1, m->m2, m->grad, m->act, m->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m;
 }
 
 int64_t hobo_mlp_num_params(hobo_mlp_h m) { return m ? m->nparam : -1; }
+
+int hobo_mlp_set_tensor_cores(hobo_mlp_h m, int on)
+{
+    if (!m) return mfail(HOBO_ERR_ARG, "NULL network");
+    if (on && !mlp_tc_supported(m->H))
+        return mfail(HOBO_ERR_UNSUPPORTED, "the tensor-core forward pass needs a hidden width of 64..256, a multiple of 64");
+    m->use_tc = on != 0;
+    return HOBO_OK;
+}
+
+int hobo_mlp_check(hobo_mlp_h m, void* stream)
+{
+    if (!m) return mfail(HOBO_ERR_ARG, "NULL network");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    int v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, m->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return mfail(HOBO_ERR_CUDA, std::string("mlp check: ") + cudaGetErrorString(e));
+    if (v != 0) {
+        const int zero = 0;
+        cudaMemcpy(m->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return mfail(HOBO_ERR_TIMEOUT, "a device-side wait of a network kernel gave up");
+    }
+    return HOBO_OK;
+}
 
 int hobo_mlp_get(hobo_mlp_h m, float* host, int rounded)
 {
@@ -385,7 +414,9 @@ int hobo_mlp_forward(hobo_mlp_h m, const float* F, int64_t n, float* logit, void
 {
     if (!m || n < 0 || (n > 0 && (!F || !logit))) return mfail(HOBO_ERR_ARG, "bad mlp forward arguments");
     if (n == 0) return HOBO_OK;
-    cudaError_t e = passes(m, F, nullptr, n, logit, nullptr, (cudaStream_t)stream);
+    cudaError_t e = m->use_tc ? launch_mlp_forward_tc(m->bf, m->H, n, F, nullptr, 0, 0.f, logit, m->status,
+                                                      (cudaStream_t)stream)
+                              : passes(m, F, nullptr, n, logit, nullptr, (cudaStream_t)stream);
     return e == cudaSuccess ? HOBO_OK : mfail(HOBO_ERR_CUDA, std::string("mlp forward: ") + cudaGetErrorString(e));
 }
 
@@ -494,9 +525,10 @@ __global__ void table_features_kernel(const float* __restrict__ beta, int S, int
 }
 
 cudaError_t mlp_tables(hobo_mlp* m, const float* beta, int S, int G, float vmax, float* tables, float* scratchF,
-                       cudaStream_t st)
+                       int* status, cudaStream_t st)
 {
     const int64_t rows = (int64_t)S * 2 * G;
+    if (m->use_tc) return launch_mlp_forward_tc(m->bf, m->H, rows, nullptr, beta, G, vmax, tables, status, st);
     table_features_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(beta, S, G, vmax, scratchF);
     cudaError_t e = cudaGetLastError();
     // forward passes over slices of rows bound the activation memory
@@ -570,7 +602,7 @@ extern "C" int hobo_anneal_learned(hobo_h h, hobo_mlp_h m, uint64_t seed, int B,
     A((void**)&d_bE, sizeof(float) * (size_t)B);
     if (learned) {
         A((void**)&tables, sizeof(float) * (size_t)std::max(sweeps, 1) * 2 * G);
-        A((void**)&tf, sizeof(float) * (size_t)std::max(sweeps, 1) * 2 * G * 3);
+        if (!m->use_tc) A((void**)&tf, sizeof(float) * (size_t)std::max(sweeps, 1) * 2 * G * 3);
     }
     if (record) A((void**)&rx, (size_t)std::max<int64_t>(nrec, 1));
     if (e == cudaSuccess && record) e = cudaMemsetAsync(rx, 0xFF, (size_t)std::max<int64_t>(nrec, 1), st);
@@ -580,7 +612,7 @@ extern "C" int hobo_anneal_learned(hobo_h h, hobo_mlp_h m, uint64_t seed, int B,
     if (e == cudaSuccess) rc = energy_dispatch(h, d_X, B, d_E, d_g, false, 0, st);
     if (e == cudaSuccess && rc == HOBO_OK && o.ev_begin) e = cudaEventRecord((cudaEvent_t)o.ev_begin, st);
     if (e == cudaSuccess && rc == HOBO_OK && learned && sweeps > 0)
-        e = mlp_tables(m, d_beta, sweeps, G, o.vmax, tables, tf, st);
+        e = mlp_tables(m, d_beta, sweeps, G, o.vmax, tables, tf, h->status, st);
     if (e == cudaSuccess && rc == HOBO_OK && sweeps > 0) {
         SweepArgs a;
         a.B = B; a.sweeps = sweeps; a.seed = seed; a.beta = d_beta;
@@ -617,5 +649,25 @@ extern "C" int hobo_anneal_learned(hobo_h h, hobo_mlp_h m, uint64_t seed, int B,
     if (rc != HOBO_OK) return rc;
     if (e != cudaSuccess) return mfail(HOBO_ERR_CUDA, std::string("learned anneal: ") + cudaGetErrorString(e));
     set_error("");
+    return HOBO_OK;
+}
+
+extern "C" int hobo_mlp_score_tables(hobo_mlp_h m, const float* beta, int S, int G, float vmax, float* tables,
+                                     void* stream)
+{
+    using namespace hobo;
+    if (!m) return mfail(HOBO_ERR_ARG, "NULL network");
+    if (S < 0) return mfail(HOBO_ERR_ARG, "negative S");
+    if (G < 2 || G > (1 << 16)) return mfail(HOBO_ERR_ARG, "G must be 2..65536");
+    if (!(vmax > 0.f) || !std::isfinite(vmax)) return mfail(HOBO_ERR_ARG, "vmax must be finite and > 0");
+    if (S == 0) return HOBO_OK;
+    if (!beta || !tables) return mfail(HOBO_ERR_ARG, "NULL beta or tables");
+    cudaStream_t st = (cudaStream_t)stream;
+    float* tf = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!m->use_tc) e = cudaMallocAsync((void**)&tf, sizeof(float) * (size_t)S * 2 * G * 3, st);
+    if (e == cudaSuccess) e = mlp_tables(m, beta, S, G, vmax, tables, tf, m->status, st);
+    if (tf) cudaFreeAsync(tf, st);
+    if (e != cudaSuccess) return mfail(HOBO_ERR_CUDA, std::string("mlp score tables: ") + cudaGetErrorString(e));
     return HOBO_OK;
 }

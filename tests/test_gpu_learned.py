@@ -43,7 +43,7 @@ def test_mlp_forward_matches_oracle():
     m = _H().MLP(hidden=256, seed=3)
     w = m.unpack(m.params(rounded=True))
     rng = np.random.default_rng(1)
-    F = _features(rng, 1000)   # 15 full 64-row tiles and a ragged one
+    F = _features(rng, 1000)   # 7 full 128-row tensor-core tiles and a ragged one
     got = m.forward(T.from_numpy(F).cuda()).cpu().numpy().astype(np.float64)
     ref = O.mlp_forward(w, F)
     # float32 sums of at most H+1 products per unit in two layers: bound the
