@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--mode", default="tuned", choices=["tuned", "plain"])
     ap.add_argument("--cpu-states", type=int, default=8, help="oracle sample size (states)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-case", default=None, choices=["sweep", "sweep-resume", "tc", "fix", "fields", "tc4", "batch", "rescore", "mlp"],
+    ap.add_argument("--kernel-case", default=None, choices=["sweep", "sweep-resume", "sweep-chunks", "tc", "fix", "fields", "tc4", "batch", "rescore",
+                             "mlp"],
                     help="run one small case of one kernel (for profilers) and exit")
     ap.add_argument("--case-states", type=int, default=4096)
     ap.add_argument("--case-sweeps", type=int, default=30)
@@ -663,6 +664,42 @@ def measure_tc4(N: int = 64, B: int = 4096):
     return out
 
 
+def sweep_chunks(inst, betas, B: int, C: int):
+    """Where the sweep kernel's time goes along the schedule."""
+    import torch
+
+    import paper_2407_19987_gb300 as H
+    h = H.Instance.from_terms(inst.idx, inst.coef, inst.N)
+    S = len(betas)
+
+    def ev():
+        return [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+
+    for _ in range(2):
+        e = ev()
+        r = h.anneal(2, B, betas, sweep_events=e, want_accepts=True)
+        torch.cuda.synchronize()
+    out = {"workload": f"{WORKLOAD}, B={B}, {S} sweeps", "whole_launch_ms": e[0].elapsed_time(e[1]),
+           "accepts": int(r["accepts"].sum().item()), "chunks": []}
+    r = None
+    for k in range(0, S, C):
+        e = ev()
+        kw = dict(sweep_events=e, want_final=True, want_fields=True, want_accepts=True)
+        if r is None:
+            r = h.anneal(2, B, betas[k:k + C], **kw)
+        else:
+            r = h.anneal(2, B, betas[k:k + C], sweep0=k, resume=True, X=r["X"], bestX=r["bestX"],
+                         bestE32=r["bestE32"], E=r["E"], g=r["g"], **kw)
+        torch.cuda.synchronize()
+        acc = r["accepts"].cpu().numpy()
+        out["chunks"].append({"sweeps": [k, min(S, k + C)], "ms": e[0].elapsed_time(e[1]), "accepts": int(acc.sum()),
+                              "accepts_max_state": int(acc.max()), "accepts_median_state": float(np.median(acc))})
+    h.check()
+    h.close()
+    print(json.dumps(out))
+    return 0
+
+
 def run_kernel_case(a):
     """One small case of one kernel, for profilers.  Dense workload: sweep:
     an anneal of --case-states states over --case-sweeps sweeps of the
@@ -676,7 +713,10 @@ def run_kernel_case(a):
     instance (N=64).  batch: the uneven batch (512 instances, 1024 states
     each) through the graph form over --case-sweeps sweeps spread over its
     schedule.  mlp: two tensor-core forward passes of the proposal network
-    (H=256) over --case-states x 256 feature rows."""
+    (H=256) over --case-states x 256 feature rows.  sweep-chunks: the whole
+    anneal's sweep kernel timed once in one launch and once as resumed
+    launches of --case-sweeps sweeps each (CUDA events), with the accepted
+    flips of each chunk; prints one JSON line."""
     import torch
 
     import paper_2407_19987_gb300 as H
@@ -705,6 +745,8 @@ def run_kernel_case(a):
         print("kernel case done: batch")
         return 0
     inst, betas, B, S = workload()
+    if a.kernel_case == "sweep-chunks":
+        return sweep_chunks(inst, betas, a.case_states, a.case_sweeps)
     if a.kernel_case == "fields":
         inst = W.sparse_order4(5000)
     elif a.kernel_case == "tc4":
