@@ -5,7 +5,7 @@
 // is the hidden H x H layer, z2 = W2 h1, which runs here as a tcgen05 MMA:
 // a tile of 128 rows (M) against all H output units (N), K = H.  Layer 1 and
 // the head are fused around it:
-//   producer warps 4-11 (two threads per row, 32 units each): h1 =
+//   producer warps 4-11 (warp: 8 units of a stage, lane: 4 rows): h1 =
 //     relu(W1 f + b1) for 64 units at a time, split into two bf16 planes h1 = hi + lo + r with
 //     hi = bf16(h1), lo = bf16(h1 - hi), |r| <= 2^-17 |h1|, written as the
 //     K-major A operand (128-byte swizzle) of one pipeline stage;
@@ -177,17 +177,22 @@ mlp_forward_tc_kernel(const MlpTcParams p)
     const float b3 = __ldg(p.w + ob3);
 
     if (warp >= 4) {
-        // ---- layer 1 into the A operand (two threads per row: units c * 8 ..
-        // c * 8 + 7 of a stage for c in half * 4 .. half * 4 + 3), MMA issue
-        // by thread 128
-        const int r = (threadIdx.x - 128) & (kMlpM - 1);
-        const int half = (threadIdx.x - 128) >> 7;
+        // ---- layer 1 into the A operand.  Producer warp c (0..7) computes
+        // units c * 8 .. c * 8 + 7 of every stage, so its weights are the
+        // same for all lanes; lane L takes the four rows
+        // (L & 7) + 8 * (4 * (L >> 3) + i), i = 0..3, so that the eight
+        // lanes storing one row's chunk position hit eight different
+        // 16-byte bank groups of the 128-byte swizzle.  MMA issue by thread 128.
+        const int c = warp - 4;
+        int rr[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rr[i] = (lane & 7) + 8 * (4 * (lane >> 3) + i);
         const uint32_t idesc = idesc_bf16(kMlpM, H);
         int cc = 0;                                   // stages used so far
         bool fail = false;
         int64_t lt = 0;
         // features of row r of a tile (zeros past the last row)
-        auto features = [&](int64_t tile, float& f0, float& f1, float& f2) {
+        auto features = [&](int64_t tile, int r, float& f0, float& f1, float& f2) {
             const int64_t row = tile * kMlpM + r;
             f0 = f1 = f2 = 0.f;
             if (tile >= p.tiles || row >= p.n) return;
@@ -205,14 +210,20 @@ mlp_forward_tc_kernel(const MlpTcParams p)
                 f2 = -logf(fmaxf(__ldg(p.beta + s), 1e-30f)) / 4.f;
             }
         };
-        float f0, f1, f2;
-        features(blockIdx.x, f0, f1, f2);
+        float f[4][3];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) features(blockIdx.x, rr[i], f[i][0], f[i][1], f[i][2]);
         for (int64_t tile = blockIdx.x; tile < p.tiles && !fail; tile += gridDim.x, ++lt) {
             const int buf = (int)(lt & 1);
             // the next tile's features load while this tile is worked on
-            float n0, n1, n2;
-            features(tile + gridDim.x, n0, n1, n2);
-            const uint64_t F0 = f32x2(f0, f0), F1 = f32x2(f1, f1), F2 = f32x2(f2, f2);
+            float nf[4][3];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) features(tile + gridDim.x, rr[i], nf[i][0], nf[i][1], nf[i][2]);
+            uint64_t F[4][3];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) F[i][k] = f32x2(f[i][k], f[i][k]);
             // the accumulator buffer is free once the epilogue has read it
             // (the first use of each buffer passes at once)
             if (!mbar_wait(&accempty[buf], (((uint32_t)lt >> 1) & 1u) ^ 1u, abort_flag)) fail = true;
@@ -223,29 +234,32 @@ mlp_forward_tc_kernel(const MlpTcParams p)
                 uint8_t* a_hi = sA + st * 32768;
                 uint8_t* a_lo = a_hi + 16384;
                 if (!fail) {
-                    const int rb = (r >> 3) * 1024 + (r & 7) * 128;
-#pragma unroll 2
-                    for (int c = half * 4; c < half * 4 + 4; ++c) {
-                        uint32_t hw[4], lw[4];
+                    uint32_t hw[4][4], lw[4][4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            // units u, u+1: z = W1 f + b1 as one fma chain per unit
-                            const int j = (kc * kMlpKC + c * 8) / 2 + e;
-                            const float4 wa = sW1[2 * j], wb = sW1[2 * j + 1];
-                            const uint64_t z = fma_f32x2(f32x2(wb.x, wb.y), F2,
-                                                         fma_f32x2(f32x2(wa.z, wa.w), F1,
-                                                                   fma_f32x2(f32x2(wa.x, wa.y), F0, f32x2(wb.z, wb.w))));
+                    for (int e = 0; e < 4; ++e) {
+                        // units u, u+1 (pair j): z = W1 f + b1 as one fma chain per unit
+                        const int j = (kc * kMlpKC + c * 8) / 2 + e;
+                        const float4 wa = sW1[2 * j], wb = sW1[2 * j + 1];
+                        const uint64_t w0 = f32x2(wa.x, wa.y), w1 = f32x2(wa.z, wa.w);
+                        const uint64_t w2 = f32x2(wb.x, wb.y), bb = f32x2(wb.z, wb.w);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const uint64_t z = fma_f32x2(w2, F[i][2], fma_f32x2(w1, F[i][1], fma_f32x2(w0, F[i][0], bb)));
                             const float h0 = fmaxf(lo_f32(z), 0.f), h1 = fmaxf(hi_f32(z), 0.f);
-                            hw[e] = pack_bf16x2(h0, h1);
+                            hw[i][e] = pack_bf16x2(h0, h1);
                             // the bf16 pair back in float32: its bits are the high halves
                             const uint64_t d = sub_f32x2(f32x2(h0, h1),
-                                                         f32x2(__uint_as_float(hw[e] << 16),
-                                                               __uint_as_float(hw[e] & 0xFFFF0000u)));
-                            lw[e] = pack_bf16x2(lo_f32(d), hi_f32(d));
+                                                         f32x2(__uint_as_float(hw[i][e] << 16),
+                                                               __uint_as_float(hw[i][e] & 0xFFFF0000u)));
+                            lw[i][e] = pack_bf16x2(lo_f32(d), hi_f32(d));
                         }
-                        const int off = rb + ((c ^ (r & 7)) << 4);
-                        *reinterpret_cast<uint4*>(a_hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        *reinterpret_cast<uint4*>(a_lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = rr[i];
+                        const int off = (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
+                        *reinterpret_cast<uint4*>(a_hi + off) = make_uint4(hw[i][0], hw[i][1], hw[i][2], hw[i][3]);
+                        *reinterpret_cast<uint4*>(a_lo + off) = make_uint4(lw[i][0], lw[i][1], lw[i][2], lw[i][3]);
                     }
                 }
                 fence_proxy_async_smem();
@@ -270,9 +284,10 @@ mlp_forward_tc_kernel(const MlpTcParams p)
                     if (kc == nKC - 1) tc_commit(&accfull[buf]);
                 }
             }
-            f0 = n0;
-            f1 = n1;
-            f2 = n2;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) f[i][k] = nf[i][k];
         }
         if (fail && threadIdx.x == 128) set_abort(abort_flag, p.status);
     } else {
