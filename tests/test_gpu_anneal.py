@@ -54,6 +54,29 @@ def test_anneal_integer_matches_oracle(name, maker, flags, B, sched, mode):
     h.close()
 
 
+WIDE_CASES = [
+    # N = 1000: the widest sparse sweep (32 words per state, 8 bits in the last word)
+    ("sparse_N1000", lambda: W.random_sparse(60, 1000, 3, 2e-5, "int"), 8, (20.0, 0.5, 4)),
+    # N = 300 with the cubic part 30 % full: the dense layout at 10 words per state
+    # (12 bits in the last word), wider than the bench instance
+    ("dense_N300", lambda: W.random_sparse(61, 300, 3, 0.3, "int", imax=2), 4, (200.0, 1.0, 2)),
+]
+
+
+@pytest.mark.parametrize("name,maker,B,sched", WIDE_CASES, ids=[c[0] for c in WIDE_CASES])
+@pytest.mark.parametrize("mode", [TUNED, PLAIN])
+def test_anneal_wide_integer_matches_oracle(name, maker, B, sched, mode):
+    inst = maker()
+    betas = W.geometric_betas(*sched)
+    h = gpuh.make(inst, 0)
+    if name.startswith("dense"):
+        assert h.info()["dense"], "expected the dense layout"
+    r = _run(h, 77, B, betas, mode)
+    ref = O.anneal(inst, 77, B, betas)
+    _compare_oracle(inst, r, ref, inst.N)
+    h.close()
+
+
 def test_paper_examples_reach_printed_ground_energies():
     """Sec. V.B / V.C: the annealer finds the printed ground energies
     (objective = energy + offset = 0)."""
