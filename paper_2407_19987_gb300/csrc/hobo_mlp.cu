@@ -35,6 +35,8 @@ struct hobo_mlp {
     // activations of a training pass, grown on demand
     float* act = nullptr;
     int64_t act_rows = 0;
+    float* part = nullptr;     // partial sums of the gradient reductions
+    size_t part_floats = 0;
     int* status = nullptr;     // device word: a bounded wait of a network kernel gave up
     bool use_tc = false;       // forward passes and score tables on the tensor cores
 };
@@ -66,24 +68,28 @@ __global__ void round_bf16_kernel(const float* __restrict__ src, float* __restri
 
 // C[M][N] = sum_k A(m,k) B(k,n), float32; A(m,k) = A[m*lda+k] (or A[k*lda+m]
 // if ta), B(k,n) = B[k*ldb+n] (or B[n*ldb+k] if tb).  64x64 tiles, 16-deep
-// K slices in shared memory, 4x4 outputs per thread, k ascending.
+// K slices in shared memory, 4x4 outputs per thread, k ascending.  Block z
+// sums k in [z * kchunk, (z + 1) * kchunk) into slice z of C (M x ldc apart).
 __global__ void __launch_bounds__(256)
 sgemm_kernel(const float* __restrict__ A, int lda, bool ta, const float* __restrict__ B, int ldb, bool tb,
-             float* __restrict__ C, int ldc, int M, int N, int K)
+             float* __restrict__ C, int ldc, int M, int N, int K, int kchunk)
 {
     __shared__ float As[16][64 + 4];
     __shared__ float Bs[16][64 + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(K, kb + kchunk);
+    C += (int64_t)blockIdx.z * M * ldc;
     float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int k0 = kb; k0 < ke; k0 += 16) {
         for (int q = threadIdx.x; q < 16 * 64; q += 256) {
             const int kk = q / 64, mm = q % 64;
             const int m = m0 + mm, k = k0 + kk;
             float a = 0.f, bv = 0.f;
-            if (m < M && k < K) a = ta ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k];
+            if (m < M && k < ke) a = ta ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k];
             const int n = n0 + mm;
-            if (n < N && k < K) bv = tb ? B[(int64_t)n * ldb + k] : B[(int64_t)k * ldb + n];
+            if (n < N && k < ke) bv = tb ? B[(int64_t)n * ldb + k] : B[(int64_t)k * ldb + n];
             As[kk][mm] = a;
             Bs[kk][mm] = bv;
         }
@@ -112,11 +118,22 @@ sgemm_kernel(const float* __restrict__ A, int lda, bool ta, const float* __restr
 }
 
 static cudaError_t sgemm(const float* A, int lda, bool ta, const float* B, int ldb, bool tb, float* C, int ldc,
-                         int M, int N, int K, cudaStream_t st)
+                         int M, int N, int K, cudaStream_t st, int splits = 1)
 {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    sgemm_kernel<<<grid, 256, 0, st>>>(A, lda, ta, B, ldb, tb, C, ldc, M, N, K);
+    const int kchunk = ((K + splits - 1) / splits + 15) / 16 * 16;
+    dim3 grid((N + 63) / 64, (M + 63) / 64, (unsigned)((K + kchunk - 1) / kchunk));
+    sgemm_kernel<<<grid, 256, 0, st>>>(A, lda, ta, B, ldb, tb, C, ldc, M, N, K, kchunk);
     return cudaGetLastError();
+}
+
+// out[i] = sum over slices z (ascending) of part[z * count + i]
+__global__ void sum_slices_kernel(const float* __restrict__ part, int S, int64_t count, float* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float s = part[i];
+    for (int z = 1; z < S; ++z) s += part[(int64_t)z * count + i];
+    out[i] = s;
 }
 
 // z1 = W1 f + b1, h1 = relu(z1)
@@ -174,46 +191,70 @@ __global__ void relu_mask_kernel(float* __restrict__ D1, const float* __restrict
     if (q < count && !(Z1[q] > 0.f)) D1[q] = 0.f;
 }
 
-// Column reductions over the rows, one thread per output, rows ascending:
-//   gb1 = sum D1, gW1[u][k] = sum D1[r][u] F[r][k], gb2 = sum D2,
-//   gw3 = sum dl H2, gb3 = sum dl, loss = sum rowloss / n
-__global__ void reduce_grads_kernel(const float* __restrict__ F, const float* __restrict__ D1,
-                                    const float* __restrict__ D2, const float* __restrict__ H2,
-                                    const float* __restrict__ dl, const float* __restrict__ rowloss, int64_t n,
-                                    int H, float* __restrict__ grad, float* __restrict__ loss)
+// Column reductions over the rows in two stages (row blocks, then the
+// blocks in order): gb1 = sum D1, gW1[u][k] = sum D1[r][u] F[r][k],
+// gb2 = sum D2, gw3 = sum dl H2, gb3 = sum dl, loss = sum rowloss / n.
+// Stage 1: block (x, z) sums rows [z * rows_per, (z + 1) * rows_per) for
+// outputs t = x * 128 + threadIdx.x into part[z][t][0..3]
+// (t < H: d, d*F0, d*F1, d*F2; H <= t < 2H: D2, dl*H2; t = 2H: dl, rowloss).
+__global__ void reduce_grads_partial_kernel(const float* __restrict__ F, const float* __restrict__ D1,
+                                            const float* __restrict__ D2, const float* __restrict__ H2,
+                                            const float* __restrict__ dl, const float* __restrict__ rowloss,
+                                            int64_t n, int H, int64_t rows_per, float4* __restrict__ part)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const MlpOff o = offsets(H);
+    if (t > 2 * H) return;
+    const int64_t r0 = (int64_t)blockIdx.z * rows_per;
+    const int64_t r1 = min(n, r0 + rows_per);
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
     if (t < H) {
-        float s = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        for (int64_t r = 0; r < n; ++r) {
+        for (int64_t r = r0; r < r1; ++r) {
             const float d = D1[r * H + t];
-            s += d;
-            a0 = fmaf(d, F[r * 3], a0);
-            a1 = fmaf(d, F[r * 3 + 1], a1);
-            a2 = fmaf(d, F[r * 3 + 2], a2);
+            a.x += d;
+            a.y = fmaf(d, F[r * 3], a.y);
+            a.z = fmaf(d, F[r * 3 + 1], a.z);
+            a.w = fmaf(d, F[r * 3 + 2], a.w);
         }
-        grad[o.b1 + t] = s;
-        grad[o.W1 + 3 * t] = a0;
-        grad[o.W1 + 3 * t + 1] = a1;
-        grad[o.W1 + 3 * t + 2] = a2;
     } else if (t < 2 * H) {
         const int v = t - H;
-        float s = 0.f, a = 0.f;
-        for (int64_t r = 0; r < n; ++r) {
-            s += D2[r * H + v];
-            a = fmaf(dl[r], H2[r * H + v], a);
+        for (int64_t r = r0; r < r1; ++r) {
+            a.x += D2[r * H + v];
+            a.y = fmaf(dl[r], H2[r * H + v], a.y);
         }
-        grad[o.b2 + v] = s;
-        grad[o.w3 + v] = a;
-    } else if (t == 2 * H) {
-        float s = 0.f, l = 0.f;
-        for (int64_t r = 0; r < n; ++r) {
-            s += dl[r];
-            l += rowloss[r];
+    } else {
+        for (int64_t r = r0; r < r1; ++r) {
+            a.x += dl[r];
+            a.y += rowloss[r];
         }
-        grad[o.b3] = s;
-        if (loss) *loss = l / (float)n;
+    }
+    part[(int64_t)blockIdx.z * (2 * H + 1) + t] = a;
+}
+
+__global__ void reduce_grads_final_kernel(const float4* __restrict__ part, int Z, int64_t n, int H,
+                                          float* __restrict__ grad, float* __restrict__ loss)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > 2 * H) return;
+    float4 a = part[t];
+    for (int z = 1; z < Z; ++z) {
+        const float4 b = part[(int64_t)z * (2 * H + 1) + t];
+        a.x += b.x;
+        a.y += b.y;
+        a.z += b.z;
+        a.w += b.w;
+    }
+    const MlpOff o = offsets(H);
+    if (t < H) {
+        grad[o.b1 + t] = a.x;
+        grad[o.W1 + 3 * t] = a.y;
+        grad[o.W1 + 3 * t + 1] = a.z;
+        grad[o.W1 + 3 * t + 2] = a.w;
+    } else if (t < 2 * H) {
+        grad[o.b2 + t - H] = a.x;
+        grad[o.w3 + t - H] = a.y;
+    } else {
+        grad[o.b3] = a.x;
+        if (loss) *loss = a.y / (float)n;
     }
 }
 
@@ -277,9 +318,36 @@ static cudaError_t passes(hobo_mlp* m, const float* F, const float* y, int64_t n
     if ((e = sgemm(D2, H, false, m->bf + o.W2, H, false, D1, H, (int)n, H, H, st)) != cudaSuccess) return e;
     relu_mask_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(D1, Z1, cnt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // gW2 = D2^T H1
-    if ((e = sgemm(D2, H, true, H1, H, false, m->grad + o.W2, H, H, H, (int)n, st)) != cudaSuccess) return e;
-    reduce_grads_kernel<<<(2 * H + 1 + 127) / 128, 128, 0, st>>>(F, D1, D2, H2, dl, rl, n, H, m->grad, loss_out);
+    // gW2 = D2^T H1, K = n split over up to 32 slices of >= 256 rows, the
+    // slices summed in order; the other gradients in row blocks of 256
+    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(32, n / 256));
+    const int64_t rows_per = 256;
+    const int Z = (int)((n + rows_per - 1) / rows_per);
+    const size_t need = std::max((size_t)splits * H * H, (size_t)Z * (2 * H + 1) * 4);
+    if (need > m->part_floats) {
+        if (m->part) cudaFree(m->part);
+        m->part = nullptr;
+        m->part_floats = 0;
+        if ((e = cudaMalloc((void**)&m->part, sizeof(float) * need)) != cudaSuccess) return e;
+        m->part_floats = need;
+    }
+    if (splits == 1) {
+        if ((e = sgemm(D2, H, true, H1, H, false, m->grad + o.W2, H, H, H, (int)n, st)) != cudaSuccess) return e;
+    } else {
+        if ((e = sgemm(D2, H, true, H1, H, false, m->part, H, H, H, (int)n, st, splits)) != cudaSuccess) return e;
+        const int64_t hh = (int64_t)H * H;
+        // the kernel may have used fewer slices than asked (16-row chunks)
+        const int kchunk = (((int)n + splits - 1) / splits + 15) / 16 * 16;
+        const int used = (int)((n + kchunk - 1) / kchunk);
+        sum_slices_kernel<<<(unsigned)((hh + 255) / 256), 256, 0, st>>>(m->part, used, hh, m->grad + o.W2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    float4* part4 = reinterpret_cast<float4*>(m->part);
+    const unsigned gx = (unsigned)((2 * H + 1 + 127) / 128);
+    // (the weight-gradient slices are consumed above before part is reused)
+    reduce_grads_partial_kernel<<<dim3(gx, 1, (unsigned)Z), 128, 0, st>>>(F, D1, D2, H2, dl, rl, n, H, rows_per, part4);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    reduce_grads_final_kernel<<<gx, 128, 0, st>>>(part4, Z, n, H, m->grad, loss_out);
     return cudaGetLastError();
 }
 
@@ -354,7 +422,7 @@ int hobo_mlp_create(hobo_mlp_h* out, int hidden, uint64_t seed)
 void hobo_mlp_destroy(hobo_mlp_h m)
 {
     if (!m) return;
-    void* ptrs[] = {m->master, m->bf, m->m1, m->m2, m->grad, m->act, m->status};
+    void* ptrs[] = {m->master, m->bf, m->m1, m->m2, m->grad, m->act, m->status, m->part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m;
