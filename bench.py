@@ -314,7 +314,7 @@ def run_ours(a):
     # DRAM bytes (read + write) of one full-size launch of the dense sweep
     # kernel, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
     # profiles/sweep_tuned_dense_N256_B4096.md); the kernel is unchanged since.
-    sweep_dram_bytes = 139011584 + 2867968
+    sweep_dram_bytes = 145923840 + 2840064
     # L2 peak of this GPU as ncu reports it: lts__t_bytes.sum.peak_sustained
     # (18048 B/cycle) x L2 clock (2.017 GHz), same profile summary.
     l2_peak_gbs = 18048 * 2.0168e9 / 1e9
