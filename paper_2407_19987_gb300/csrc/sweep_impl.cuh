@@ -67,7 +67,6 @@ __device__ __forceinline__ void set_word(uint32_t (&x)[WMAX], int w, uint32_t v)
 // updated by the whole warp) and the word is re-evaluated from f + 1.  This
 // is exactly the sequential order of the definition.
 // ---------------------------------------------------------------------------
-constexpr int kSweepWarps = 8;
 // Warps per CTA of the single-instance sweep.  One-warp CTAs let the block
 // scheduler spread the states evenly over the SMs (4096 states are 27 warps
 // per SM); measured 17% faster than 8-warp CTAs on the order-4 workload and
@@ -675,13 +674,15 @@ __device__ __forceinline__ void anneal_state_learned(const SweepDev& p, const Le
     }
 }
 
+// Same launch shape as the tuned sweep: one-warp CTAs, at least 27 resident
+// per SM.
 template <int WMAX, bool DENSE, int KU>
-__global__ void __launch_bounds__(kSweepWarps * 32, 4)
+__global__ void __launch_bounds__(kTunedWarps * 32, kTunedMinBlocks)
 sweep_learned_kernel(const SweepDev p, const LearnedDev L)
 {
     extern __shared__ float sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int b = blockIdx.x * kSweepWarps + warp;
+    const int b = blockIdx.x * kTunedWarps + warp;
     if (b >= p.B) return;
     anneal_state_learned<WMAX, DENSE, KU>(p, L, b, sm + (size_t)warp * learned_region_floats(p.N, WMAX), lane);
 }
@@ -689,11 +690,11 @@ sweep_learned_kernel(const SweepDev p, const LearnedDev L)
 template <int WMAX, bool DENSE, int KU>
 inline cudaError_t run_learned(const SweepDev& p, const LearnedDev& L, cudaStream_t st)
 {
-    const size_t sm = sizeof(float) * (size_t)learned_region_floats(p.N, WMAX) * kSweepWarps;
+    const size_t sm = sizeof(float) * (size_t)learned_region_floats(p.N, WMAX) * kTunedWarps;
     auto kern = sweep_learned_kernel<WMAX, DENSE, KU>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)((p.B + kSweepWarps - 1) / kSweepWarps), kSweepWarps * 32, sm, st>>>(p, L);
+    kern<<<(unsigned)((p.B + kTunedWarps - 1) / kTunedWarps), kTunedWarps * 32, sm, st>>>(p, L);
     return cudaGetLastError();
 }
 
