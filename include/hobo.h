@@ -57,7 +57,7 @@ extern "C" {
                                  coefficients; exact for float32 values) */
 #define HOBO_SPLIT2      16u  /* tensor-core energy: hi+lo bf16 split for
                                  non-integer coefficients (relative error per
-                                 coefficient <= 2^-17; faster, below the
+                                 coefficient <= 2^-16; faster, below the
                                  1e-5 bar on ill-conditioned fields).  Integer
                                  coefficients below 2^16 always use hi+lo,
                                  which is exact for them. */
@@ -330,7 +330,7 @@ int hobo_mlp_set(hobo_mlp_h m, const float* host);
 /* Logits of n feature rows F (device [n][3]) into logit (device [n]).
  * Networks of hidden width 64..256 (a multiple of 64) run the H x H layer
  * on the tensor cores (tcgen05: hidden activations split into two bf16
- * planes hi + lo, relative residual <= 2^-17, against the bf16 weights,
+ * planes hi + lo, relative residual <= 2^-16, against the bf16 weights,
  * float32 accumulation), with layer 1 and the head fused around it; other
  * widths run float32 CUDA-core passes.  The score tables of
  * hobo_anneal_learned use the same pass.  Errors: HOBO_ERR_ARG,

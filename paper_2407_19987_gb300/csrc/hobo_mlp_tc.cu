@@ -7,7 +7,7 @@
 // the head are fused around it:
 //   producer warps 4-11 (warp: 8 units of a stage, lane: 4 rows): h1 =
 //     relu(W1 f + b1) for 64 units at a time, split into two bf16 planes h1 = hi + lo + r with
-//     hi = bf16(h1), lo = bf16(h1 - hi), |r| <= 2^-17 |h1|, written as the
+//     hi = bf16(h1), lo = bf16(h1 - hi), |r| <= 2^-16 |h1|, written as the
 //     K-major A operand (128-byte swizzle) of one pipeline stage;
 //   thread 128 issues, per stage, the MMAs of both planes against the bf16
 //     W2 slab (resident in shared memory for the whole kernel): the bf16 x

@@ -10,7 +10,7 @@ import pytest
 import gpuh
 import workloads as W
 from oracle import oracle as O
-from test_gpu_learned import CASES, _abs_net, _compare, _features, _set_net
+from test_gpu_learned import CASES, _abs_net, _compare, _features, _set_net, tol_cuda_cores, tol_tensor_cores
 from test_oracle_mlp import identity_net
 
 pytestmark = pytest.mark.gpu
@@ -19,13 +19,6 @@ pytestmark = pytest.mark.gpu
 def _H():
     import paper_2407_19987_gb300 as H
     return H
-
-
-# the hidden activations enter the tensor cores as two bf16 planes hi + lo
-# (relative residual <= 2^-18 each); with float32 sums of H+1 products per
-# unit in two layers the error stays below 2e-5 (2^-15.6) of the same
-# network run on magnitudes, the bound the CUDA-core pass meets too
-TOL = 2e-5
 
 
 @pytest.mark.parametrize("H", [64, 128, 192, 256])
@@ -43,22 +36,22 @@ def test_tensor_core_forward_matches_oracle(H, n):
     m.check()
     ref = O.mlp_forward(w, F)
     scale = O.mlp_forward(_abs_net(w), np.abs(F))
-    assert np.all(np.abs(got - ref) <= TOL * scale)
+    assert np.all(np.abs(got - ref) <= tol_tensor_cores(H) * scale)
     m.set_tensor_cores(False)
     cc = m.forward(Fd).cpu().numpy().astype(np.float64)
-    assert np.all(np.abs(cc - ref) <= TOL * scale)
+    assert np.all(np.abs(cc - ref) <= tol_cuda_cores(H) * scale)
     m.close()
 
 
 def test_tensor_core_forward_of_special_networks():
-    """The identity network gives logit = f0 up to the two-plane split;
+    """The identity network gives logit = f0 up to the two-plane split (2^-16);
     a network with W2 = 0 gives b3 + sum w3 relu(b2) exactly on every row."""
     T = gpuh.torch()
     rng = np.random.default_rng(3)
     F = _features(rng, 300)
     m = _set_net(identity_net(64), 64)
     got = m.forward(T.from_numpy(F).cuda()).cpu().numpy().astype(np.float64)
-    np.testing.assert_allclose(got, F[:, 0].astype(np.float64), rtol=2.0 ** -17, atol=0)
+    np.testing.assert_allclose(got, F[:, 0].astype(np.float64), rtol=2.0 ** -16, atol=0)
     m.close()
     w = identity_net(128)
     w["W2"][:] = 0.0
@@ -95,10 +88,11 @@ def test_score_tables_match_oracle_network(H, G):
     F = F.reshape(-1, 3)
     ref = O.mlp_forward(w, F).reshape(S, 2, G)
     scale = O.mlp_forward(_abs_net(w), np.abs(F)).reshape(S, 2, G)
-    assert np.all(np.abs(tab - ref) <= TOL * scale + 1e-6)
+    # (+1e-6: the kernel forms -ln(beta)/4 in float32 from the float32 beta)
+    assert np.all(np.abs(tab - ref) <= tol_tensor_cores(H) * scale + 1e-6)
     m.set_tensor_cores(False)
     cc = m.score_tables(T.from_numpy(betas).cuda(), G, vmax).cpu().numpy().astype(np.float64)
-    assert np.all(np.abs(cc - ref) <= TOL * scale + 1e-6)
+    assert np.all(np.abs(cc - ref) <= tol_cuda_cores(H) * scale + 1e-6)
     m.close()
 
 
@@ -130,7 +124,7 @@ SELECTS_TC = [(3, 0, 1.0, 0.0), (2, 0, 0.1, 0.0), (3, 1, 1.0, -1e-3)]
 def test_learned_anneal_with_tensor_core_tables_matches_oracle(name, maker, flags, B, sched, plain_every, select,
                                                                top_frac, threshold):
     """Identity network of width 64 (tables from the tensor-core pass): the
-    two-plane residual (<= 2^-17 of a score) is far below the beta/8 gap
+    two-plane residual (<= 2^-16 of a score) is far below the beta/8 gap
     between distinct scores on integer instances and below the distance of
     every score to the threshold -1e-3, so selections equal the oracle's."""
     inst = maker()
