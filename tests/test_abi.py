@@ -103,3 +103,47 @@ def test_null_instance_calls(lib):
     assert lib.hobo_anneal(None, 0, 0, None, 0, None, None, None, None) == Bd.HOBO_ERR_ARG
     assert lib.hobo_info(None, None) == Bd.HOBO_ERR_ARG
     lib.hobo_destroy(None)
+
+
+def test_null_handles_and_bad_arguments_of_the_other_entry_points(lib):
+    """Network, tensor-train, batch and result-table calls refuse NULL
+    handles and out-of-range arguments before any device work."""
+    ARG = Bd.HOBO_ERR_ARG
+    h = C.c_void_p()
+    # network
+    assert lib.hobo_mlp_create(C.byref(h), 33, C.c_uint64(0)) == ARG            # not a multiple of 32
+    assert lib.hobo_mlp_create(C.byref(h), 2048, C.c_uint64(0)) == ARG
+    assert lib.hobo_mlp_create(None, 64, C.c_uint64(0)) == ARG
+    assert lib.hobo_mlp_num_params(None) == -1
+    assert lib.hobo_mlp_get(None, None, 1) == ARG
+    assert lib.hobo_mlp_set(None, None) == ARG
+    assert lib.hobo_mlp_forward(None, None, 1, None, None) == ARG
+    assert lib.hobo_mlp_score_tables(None, None, 1, 16, C.c_float(32.0), None, None) == ARG
+    assert lib.hobo_mlp_set_tensor_cores(None, 1) == ARG
+    assert lib.hobo_mlp_check(None, None) == ARG
+    assert lib.hobo_mlp_loss_grad(None, None, None, 1, None, None, None) == ARG
+    assert lib.hobo_mlp_train_step(None, None, None, 1, C.c_float(1e-3), None, None) == ARG
+    assert lib.hobo_mlp_save(None, b"x") == ARG
+    assert lib.hobo_mlp_load(C.byref(h), b"/nonexistent/net.bin") == ARG
+    assert lib.hobo_anneal_learned(None, None, C.c_uint64(0), 1, None, 0, None, None, None, None) == ARG
+    lib.hobo_mlp_destroy(None)
+    # tensor train
+    ranks = (C.c_int * 3)(1, 2, 1)
+    cores = np.zeros(64, np.float32)
+    assert lib.hobo_tt_create(None, 2, 4, ranks, cores.ctypes.data_as(C.c_void_p)) == ARG
+    assert lib.hobo_tt_create(C.byref(h), 0, 4, ranks, cores.ctypes.data_as(C.c_void_p)) == Bd.HOBO_ERR_ORDER
+    bad = (C.c_int * 3)(2, 2, 1)                                                # ranks[0] must be 1
+    assert lib.hobo_tt_create(C.byref(h), 2, 4, bad, cores.ctypes.data_as(C.c_void_p)) == ARG
+    assert lib.hobo_tt_create(C.byref(h), 2, 4, ranks, None) == ARG
+    assert lib.hobo_tt_energy(None, None, 1, None, None) == ARG
+    lib.hobo_tt_destroy(None)
+    # batches
+    assert lib.hobo_batch_create(None, None, 1, None) == ARG
+    assert lib.hobo_batch_create(C.byref(h), None, 0, None) == ARG
+    assert lib.hobo_batch_layout(None, None, None) == ARG
+    assert lib.hobo_batch_anneal(None, None, None, 0, None, None, None, None) == ARG
+    assert lib.hobo_batch_launch_shape(None, 0, None, None) == ARG
+    # result table
+    assert lib.hobo_aggregate(0, None, None, 1, None, None, None, None, None, None) == ARG   # W
+    assert lib.hobo_aggregate(1, None, None, -1, None, None, None, None, None, None) == ARG  # B
+    assert lib.hobo_aggregate(1, None, None, 4, None, None, None, None, None, None) == ARG   # K NULL
