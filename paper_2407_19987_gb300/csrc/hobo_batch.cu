@@ -277,7 +277,7 @@ using namespace hobo;
 
 extern "C" {
 
-int hobo_batch_create(hobo_batch_h* out, const hobo_h* hs, int n, const int* B)
+static int hobo_batch_create_impl(hobo_batch_h* out, const hobo_h* hs, int n, const int* B)
 {
     if (!out) return bfail(HOBO_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -365,6 +365,11 @@ int hobo_batch_create(hobo_batch_h* out, const hobo_h* hs, int n, const int* B)
     return HOBO_OK;
 }
 
+int hobo_batch_create(hobo_batch_h* out, const hobo_h* hs, int n, const int* B)
+{
+    return hobo::guarded("hobo_batch_create", [&] { return hobo_batch_create_impl(out, hs, n, B); });
+}
+
 void hobo_batch_destroy(hobo_batch_h bh)
 {
     if (!bh) return;
@@ -382,8 +387,8 @@ int hobo_batch_layout(hobo_batch_h bh, int64_t* state_offset, int64_t* word_offs
     return HOBO_OK;
 }
 
-int hobo_batch_anneal(hobo_batch_h bh, const uint64_t* seeds, const float* beta, int sweeps,
-                      uint32_t* bestX, double* bestE, const hobo_batch_opts* opts, void* stream)
+static int hobo_batch_anneal_impl(hobo_batch_h bh, const uint64_t* seeds, const float* beta, int sweeps,
+                                  uint32_t* bestX, double* bestE, const hobo_batch_opts* opts, void* stream)
 {
     if (!bh) return bfail(HOBO_ERR_ARG, "NULL batch");
     if (!seeds || sweeps < 0 || (sweeps > 0 && !beta) || !bestX || !bestE)
@@ -449,6 +454,12 @@ int hobo_batch_anneal(hobo_batch_h bh, const uint64_t* seeds, const float* beta,
     if (e != cudaSuccess) return bfail(HOBO_ERR_CUDA, "output copy");
     set_error("");
     return HOBO_OK;
+}
+
+int hobo_batch_anneal(hobo_batch_h bh, const uint64_t* seeds, const float* beta, int sweeps,
+                      uint32_t* bestX, double* bestE, const hobo_batch_opts* opts, void* stream)
+{
+    return hobo::guarded("hobo_batch_anneal", [&] { return hobo_batch_anneal_impl(bh, seeds, beta, sweeps, bestX, bestE, opts, stream); });
 }
 
 int hobo_batch_launch_shape(hobo_batch_h bh, int group, int* warps_per_cta, int* ctas)

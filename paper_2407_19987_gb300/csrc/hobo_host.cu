@@ -595,7 +595,7 @@ int hobo::energy_dispatch(const hobo_instance* h, const uint32_t* X, int B, floa
 
 extern "C" {
 
-int hobo_create(hobo_h* out, const float* T, int order, int N, unsigned flags)
+static int hobo_create_impl(hobo_h* out, const float* T, int order, int N, unsigned flags)
 {
     if (!out) return fail(HOBO_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -625,8 +625,13 @@ int hobo_create(hobo_h* out, const float* T, int order, int N, unsigned flags)
     return create_from_entries(out, ent, order, N, flags);
 }
 
-int hobo_create_terms(hobo_h* out, const int32_t* idx, const float* coef, int64_t nnz, int order,
-                      int N, unsigned flags)
+int hobo_create(hobo_h* out, const float* T, int order, int N, unsigned flags)
+{
+    return hobo::guarded("hobo_create", [&] { return hobo_create_impl(out, T, order, N, flags); });
+}
+
+static int hobo_create_terms_impl(hobo_h* out, const int32_t* idx, const float* coef, int64_t nnz, int order,
+                                  int N, unsigned flags)
 {
     if (!out) return fail(HOBO_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -648,6 +653,12 @@ int hobo_create_terms(hobo_h* out, const int32_t* idx, const float* coef, int64_
         ent.push_back(e);
     }
     return create_from_entries(out, ent, order, N, flags);
+}
+
+int hobo_create_terms(hobo_h* out, const int32_t* idx, const float* coef, int64_t nnz, int order,
+                      int N, unsigned flags)
+{
+    return hobo::guarded("hobo_create_terms", [&] { return hobo_create_terms_impl(out, idx, coef, nnz, order, N, flags); });
 }
 
 void hobo_destroy(hobo_h h)

@@ -1,6 +1,8 @@
 // Internal declarations shared by the host library and the kernel files.
 #pragma once
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 #include <cuda_runtime.h>
 #include "hobo.h"
@@ -164,6 +166,26 @@ cudaError_t launch_mlp_forward_tc(const float* w, int H, int64_t n, const float*
                                   float vmax, float* out, int* status, cudaStream_t st);
 
 void set_error(const std::string& msg);
+
+// Runs an entry point's body so that no C++ exception crosses the C ABI: a
+// failed host allocation returns HOBO_ERR_OOM, any other exception (e.g. a
+// container length error from absurd sizes) HOBO_ERR_ARG, with a message.
+template <class F>
+int guarded(const char* what, F&& body)
+{
+    try {
+        return body();
+    } catch (const std::bad_alloc&) {
+        set_error(std::string(what) + ": host allocation failed");
+        return HOBO_ERR_OOM;
+    } catch (const std::exception& e) {
+        set_error(std::string(what) + ": " + e.what());
+        return HOBO_ERR_ARG;
+    } catch (...) {
+        set_error(std::string(what) + ": unexpected error");
+        return HOBO_ERR_ARG;
+    }
+}
 
 // Energy/field contraction with the automatic or explicit path (0 auto,
 // 1 term list, 2 tensor core); returns a HOBO_* status.

@@ -378,7 +378,7 @@ using namespace hobo;
 
 extern "C" {
 
-int hobo_mlp_create(hobo_mlp_h* out, int hidden, uint64_t seed)
+static int hobo_mlp_create_impl(hobo_mlp_h* out, int hidden, uint64_t seed)
 {
     if (!out) return mfail(HOBO_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -417,6 +417,11 @@ int hobo_mlp_create(hobo_mlp_h* out, int hidden, uint64_t seed)
     }
     *out = m;
     return HOBO_OK;
+}
+
+int hobo_mlp_create(hobo_mlp_h* out, int hidden, uint64_t seed)
+{
+    return hobo::guarded("hobo_mlp_create", [&] { return hobo_mlp_create_impl(out, hidden, seed); });
 }
 
 void hobo_mlp_destroy(hobo_mlp_h m)
@@ -516,7 +521,7 @@ int hobo_mlp_train_step(hobo_mlp_h m, const float* F, const float* y, int64_t n,
 
 // Checkpoint: a one-line JSON header, then the bf16 weights (little-endian
 // uint16, flat layout above).
-int hobo_mlp_save(hobo_mlp_h m, const char* path)
+static int hobo_mlp_save_impl(hobo_mlp_h m, const char* path)
 {
     if (!m || !path) return mfail(HOBO_ERR_ARG, "NULL argument");
     std::vector<float> w((size_t)m->nparam);
@@ -536,7 +541,12 @@ int hobo_mlp_save(hobo_mlp_h m, const char* path)
     return wr == b.size() ? HOBO_OK : mfail(HOBO_ERR_ARG, "short write");
 }
 
-int hobo_mlp_load(hobo_mlp_h* out, const char* path)
+int hobo_mlp_save(hobo_mlp_h m, const char* path)
+{
+    return hobo::guarded("hobo_mlp_save", [&] { return hobo_mlp_save_impl(m, path); });
+}
+
+static int hobo_mlp_load_impl(hobo_mlp_h* out, const char* path)
 {
     if (!out || !path) return mfail(HOBO_ERR_ARG, "NULL argument");
     *out = nullptr;
@@ -570,6 +580,11 @@ int hobo_mlp_load(hobo_mlp_h* out, const char* path)
     if (rc) { hobo_mlp_destroy(m); return rc; }
     *out = m;
     return HOBO_OK;
+}
+
+int hobo_mlp_load(hobo_mlp_h* out, const char* path)
+{
+    return hobo::guarded("hobo_mlp_load", [&] { return hobo_mlp_load_impl(out, path); });
 }
 
 }  // extern "C"

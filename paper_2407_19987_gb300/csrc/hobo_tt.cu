@@ -139,7 +139,7 @@ using namespace hobo;
 
 extern "C" {
 
-int hobo_tt_create(hobo_tt_h* out, int order, int N, const int* ranks, const float* cores)
+static int hobo_tt_create_impl(hobo_tt_h* out, int order, int N, const int* ranks, const float* cores)
 {
     if (!out) return tfail(HOBO_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -187,6 +187,11 @@ int hobo_tt_create(hobo_tt_h* out, int order, int N, const int* ranks, const flo
     *out = t;
     set_error("");
     return HOBO_OK;
+}
+
+int hobo_tt_create(hobo_tt_h* out, int order, int N, const int* ranks, const float* cores)
+{
+    return hobo::guarded("hobo_tt_create", [&] { return hobo_tt_create_impl(out, order, N, ranks, cores); });
 }
 
 void hobo_tt_destroy(hobo_tt_h t)

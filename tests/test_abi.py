@@ -147,3 +147,17 @@ def test_null_handles_and_bad_arguments_of_the_other_entry_points(lib):
     assert lib.hobo_aggregate(0, None, None, 1, None, None, None, None, None, None) == ARG   # W
     assert lib.hobo_aggregate(1, None, None, -1, None, None, None, None, None, None) == ARG  # B
     assert lib.hobo_aggregate(1, None, None, 4, None, None, None, None, None, None) == ARG   # K NULL
+
+
+def test_no_exception_crosses_the_abi(lib):
+    """A term count no host container can hold is refused with an error code
+    (the reservation fails before any index is read) instead of an
+    exception escaping the C interface."""
+    h = C.c_void_p()
+    idx = np.zeros(3, np.int32)
+    coef = np.ones(1, np.float32)
+    rc = lib.hobo_create_terms(C.byref(h), idx.ctypes.data_as(C.c_void_p), coef.ctypes.data_as(C.c_void_p),
+                               C.c_int64(1 << 62), 3, 10, 0)
+    assert rc in (Bd.HOBO_ERR_ARG, Bd.HOBO_ERR_OOM)
+    assert h.value is None
+    assert b"hobo_create_terms" in lib.hobo_last_error()
