@@ -244,3 +244,33 @@ def test_state_offset_shards_reproduce_one_call(maker, flags, mode):
         ref = O.anneal(inst, 9, 37, betas, state0=33)
         np.testing.assert_array_equal(parts[1]["bestE"].cpu().numpy(), ref["bestE"])
     h.close()
+
+
+DEGENERATE = [
+    ("N1_order1", lambda: W.random_sparse(80, 1, 1, 0.0, "int")),           # one variable, E = a x
+    ("order1_N40", lambda: W.random_sparse(81, 40, 1, 0.0, "int")),         # no interactions: fields constant
+    ("complete_N2_order2", lambda: W.dense_all_degrees(82, 2, 2, "int")),
+    ("complete_N3_order3", lambda: W.dense_all_degrees(83, 3, 3, "int")),
+]
+
+
+@pytest.mark.parametrize("name,maker", DEGENERATE, ids=[c[0] for c in DEGENERATE])
+@pytest.mark.parametrize("mode", [TUNED, PLAIN])
+def test_anneal_degenerate_instances_match_oracle(name, maker, mode):
+    """The smallest instances the method has: trajectories bit-exact against
+    the oracle (33 states: one full warp and a ragged one), and energies and
+    flip deltas of every state of the small ones against brute force."""
+    inst = maker()
+    betas = W.geometric_betas(5.0, 0.05, 20)
+    h = gpuh.make(inst, 0)
+    r = _run(h, 5, 33, betas, mode)
+    ref = O.anneal(inst, 5, 33, betas)
+    _compare_oracle(inst, r, ref, inst.N)
+    if inst.N <= 3:
+        T = gpuh.torch()
+        X = np.array([[(s >> i) & 1 for i in range(inst.N)] for s in range(1 << inst.N)], np.uint8)
+        E, dE = h.energy(T.from_numpy(W.pack_bits(X).view(np.int32)).cuda())
+        np.testing.assert_array_equal(E.cpu().numpy().astype(np.int64), O.energy_int(inst, X))
+        for s in range(1 << inst.N):
+            np.testing.assert_array_equal(dE[s].cpu().numpy().astype(np.float64), O.flip_delta(inst, X[s]))
+    h.close()

@@ -140,3 +140,19 @@ def test_learned_anneal_with_tensor_core_tables_matches_oracle(name, maker, flag
     _compare(r, ref, inst.N)
     h.close()
     m.close()
+
+
+@pytest.mark.parametrize("H", [32, 1024])
+def test_cuda_core_forward_at_the_smallest_and_largest_width(H):
+    """Widths the tensor-core pass does not take run the float32 passes."""
+    T = gpuh.torch()
+    m = _H().MLP(hidden=H, seed=H)
+    with pytest.raises(_H().HoboError):
+        m.set_tensor_cores(True)
+    w = m.unpack(m.params(rounded=True))
+    F = _features(np.random.default_rng(H), 300)
+    got = m.forward(T.from_numpy(F).cuda()).cpu().numpy().astype(np.float64)
+    ref = O.mlp_forward(w, F)
+    scale = O.mlp_forward(_abs_net(w), np.abs(F))
+    assert np.all(np.abs(got - ref) <= tol_cuda_cores(H) * scale)
+    m.close()
