@@ -284,3 +284,23 @@ def test_trained_network_gain_over_the_sweep_without_it():
         print(f"seed {seed}: mean best plain {Et.mean():.2f} ({ms_t:.1f} ms), learned {El.mean():.2f} ({ms_l:.1f} ms)")
         h.close()
     assert all(abs(r) < 0.02 for r in rel), rel
+
+
+@pytest.mark.parametrize("name,maker", [("N1_order1", lambda: W.random_sparse(80, 1, 1, 0.0, "int")),
+                                        ("complete_N3_order3", lambda: W.dense_all_degrees(83, 3, 3, "int"))],
+                         ids=["N1_order1", "complete_N3_order3"])
+@pytest.mark.parametrize("select", [0, 1])
+def test_learned_anneal_degenerate_instances_match_oracle(name, maker, select):
+    """One variable, and a complete three-variable instance: the learned
+    sweep sorts or filters keys of which all but one or three are padding."""
+    inst = maker()
+    betas = W.geometric_betas(5.0, 0.05, 12)
+    h = gpuh.make(inst)
+    w = identity_net()
+    m = _set_net(w)
+    r = _H().anneal_learned(h, m, 5, 33, betas, plain_every=3, select=select, top_frac=1.0, threshold=-1e-3,
+                            want_final=True, want_accepts=True)
+    ref = O.anneal_learned(inst, 5, 33, betas, w, plain_every=3, select=select, top_frac=1.0, threshold=-1e-3)
+    _compare(r, ref, inst.N)
+    h.close()
+    m.close()
