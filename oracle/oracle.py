@@ -1,9 +1,18 @@
-"""ctypes wrapper of the CPU oracle (hobo_oracle.c).
+"""The CPU oracle: a ctypes wrapper of hobo_oracle.c plus the result table
+and tensor-train routines in numpy.
 
 Test infrastructure only: the tests, the package smoke check and the
 benchmark's CPU-baseline leg may import this module; the product path never
-does.  Everything here is a thin marshalling layer over the C routines,
-which state the arithmetic and its sources.
+does.  The energy, field, random-number, annealing and network routines are
+thin marshalling over the C code, which states their arithmetic and
+sources.  Written here in numpy, each citing its passage:
+  aggregate            the result table of a run (Sec. V: states by energy
+                       with occurrence counts); pinned by a hand example and
+                       by direct scans on random pools.
+  tt_svd, tt_full,     tensor-train decomposition and contraction (Sec. VI);
+  tt_energy            pinned by the TSP tensor's printed bond dimensions,
+                       the printed einsum path cost, rank-1 closed forms and
+                       brute force against the full tensor.
 """
 from __future__ import annotations
 
