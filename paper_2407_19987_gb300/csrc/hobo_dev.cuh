@@ -46,39 +46,22 @@ __device__ __forceinline__ uint32_t pick4(const u32x4& r, int k)
 //          coefficients rounded to float, Horner order)
 //   result = p * 2^n, 2^n assembled in the exponent field (n >= -125 keeps
 //   the product normal, so the scaling is exact).
-// Relative error against 2^t is below 4e-7 on [-125, 0].
+// Relative error against 2^t is below 4e-7 on [-125, 0].  Evaluated without
+// branches: arguments below -125 give 0 by a select, so that the 32 lanes
+// of a warp never take different paths.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float exp2_fixed(float t)
 {
-    if (!(t >= -125.0f)) return 0.0f;
-    const float n = floorf(__fadd_rn(t, 0.5f));
-    const float f = __fsub_rn(t, n);
+    const bool under = !(t >= -125.0f);
+    const float tc = under ? 0.0f : t;
+    const float n = floorf(__fadd_rn(tc, 0.5f));
+    const float f = __fsub_rn(tc, n);
     float p = __uint_as_float(0x39218489u);                       // (ln2)^6/720
     p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3AAEC3FFu)); // (ln2)^5/120
     p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3C1D955Bu)); // (ln2)^4/24
     p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3D635847u)); // (ln2)^3/6
     p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3E75FDF0u)); // (ln2)^2/2
     p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3F317218u)); // ln2
-    p = __fadd_rn(__fmul_rn(p, f), 1.0f);
-    const int ni = (int)n;
-    return __fmul_rn(p, __uint_as_float((uint32_t)(ni + 127) << 23));
-}
-
-// The same sequence without branches: arguments below -125 give 0 by a
-// select instead of an early return, so that the 32 lanes of a warp never
-// take different paths.
-__device__ __forceinline__ float exp2_fixed_nb(float t)
-{
-    const bool under = !(t >= -125.0f);
-    const float tc = under ? 0.0f : t;
-    const float n = floorf(__fadd_rn(tc, 0.5f));
-    const float f = __fsub_rn(tc, n);
-    float p = __uint_as_float(0x39218489u);
-    p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3AAEC3FFu));
-    p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3C1D955Bu));
-    p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3D635847u));
-    p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3E75FDF0u));
-    p = __fadd_rn(__fmul_rn(p, f), __uint_as_float(0x3F317218u));
     p = __fadd_rn(__fmul_rn(p, f), 1.0f);
     const int ni = (int)n;
     const float r = __fmul_rn(p, __uint_as_float((uint32_t)(ni + 127) << 23));
@@ -94,7 +77,7 @@ __device__ __forceinline__ bool metropolis(float dE, float beta, uint32_t w)
 {
     const float a = __fmul_rn(beta, dE);
     const float t = fminf(-__fmul_rn(a, __uint_as_float(0x3FB8AA3Bu)), 0.0f);   // log2(e)
-    const float p = exp2_fixed_nb(t);
+    const float p = exp2_fixed(t);
     const float u = __fmul_rn((float)(w >> 8), 5.9604644775390625e-8f);  // 2^-24
     return (dE <= 0.0f) | (u < p);
 }
@@ -124,13 +107,8 @@ __device__ __forceinline__ uint32_t bit_of(const uint32_t* words, int i)
     return (words[i >> 5] >> (i & 31)) & 1u;
 }
 
-// Bounded device-side waits give up after this many polls and report
-// HOBO_ERR_TIMEOUT through the status word.
-constexpr long long kSpinLimit = 1ll << 26;
-
-// Status word codes written by kernels (host maps them to HOBO_ERR_*).
-constexpr int kDevOk = 0;
+// Status word code a kernel writes when a bounded device-side wait gave up
+// (0 = none); hobo_check / hobo_mlp_check report it as HOBO_ERR_TIMEOUT.
 constexpr int kDevTimeout = 1;
-constexpr int kDevBadArg = 2;
 
 }  // namespace hobo
