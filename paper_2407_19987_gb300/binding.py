@@ -225,11 +225,12 @@ class Instance:
         B = X.shape[0]
         E = torch.empty(B, dtype=torch.float32, device=X.device)
         dE = torch.empty((B, self.N), dtype=torch.float32, device=X.device) if with_delta else None
-        _check(load_library().hobo_energy_path(self._h, _ptr(X), B, _ptr(E), _ptr(dE), path,
-                                               _stream(stream)))
+        self.energy_into(X, E, dE, path, stream)
         return E, dE
 
     def energy_into(self, X, E, dE=None, path: int = PATH_AUTO, stream=None):
+        """hobo_energy_path into caller buffers: E float32 CUDA [B], dE float32
+        CUDA [B, N] or None (no flip deltas)."""
         _check(load_library().hobo_energy_path(self._h, _ptr(X), X.shape[0], _ptr(E), _ptr(dE), path,
                                                _stream(stream)))
 
