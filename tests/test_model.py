@@ -77,3 +77,33 @@ def test_compile_refuses_inexact_coefficients():
     assert m.compile((2 ** 25 + 1) * x, exact=False).coef[0] == np.float32(2 ** 25)
     with pytest.raises(TypeError):
         x + "a"
+
+
+def test_msb_first_encoding_dense_form_and_refusals():
+    m = Model()
+    y = m.integer("y", 3, msb_first=True)                    # y = 4 b0 + 2 b1 + b2
+    x = m.binary("x")
+    c = m.compile(y * x - 2 * y + 7)
+    assert c.offset == 7 and c.order == 2
+    ids, weights, lower = c.integers["y"]
+    assert weights == [4, 2, 1] and lower == 0
+    bits = np.zeros(c.N, np.int64)
+    bits[ids[0]] = bits[ids[2]] = 1
+    assert c.decode(bits)["y"] == 5
+    # the dense upper-triangular tensor holds the same energy as the entries
+    X = np.array([[(s >> i) & 1 for i in range(c.N)] for s in range(1 << c.N)], np.uint8)
+    T = c.dense()
+    dense_E = np.einsum("ij,bi,bj->b", T, X.astype(np.float64), X.astype(np.float64))
+    np.testing.assert_array_equal(dense_E, O.energy(_as_instance(c), X))
+    # objective value = energy + offset, checked against direct evaluation
+    Xi = X.astype(np.int64)
+    yv = 4 * Xi[:, ids[0]] + 2 * Xi[:, ids[1]] + Xi[:, ids[2]]
+    np.testing.assert_array_equal(dense_E + c.offset, yv * Xi[:, c.groups["x"]] - 2 * yv + 7)
+    assert x ** 0 == 1 and (x ** 3) == x
+    with pytest.raises(ValueError):
+        m.binary("x")                                          # name already declared
+    other = Model()
+    other.binary("u", (5,))
+    w = other.binary("w")
+    with pytest.raises(ValueError):
+        m.compile(w)                                           # index beyond this model's variables
