@@ -7,7 +7,7 @@
 // loops that must not risk the implicit synchronisation or the pool growth
 // an allocation can bring.  For them this entry point keeps its scratch, the
 // 64-bit integer accumulators of the re-score, in a fixed array in device
-// memory declared at file scope, which the driver sets aside once for every
+// memory declared at file scope, which the CUDA driver sets aside once for every
 // GPU that loads the library and keeps until the process exits.
 //
 // Every call shares that one array per device, and the array keeps whatever
