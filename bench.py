@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--mode", default="tuned", choices=["tuned", "plain"])
     ap.add_argument("--cpu-states", type=int, default=8, help="oracle sample size (states)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-case", default=None, choices=["sweep", "sweep-resume", "sweep-chunks", "tc", "fix", "fields", "tc4", "batch", "rescore",
+    ap.add_argument("--kernel-case", default=None, choices=["sweep", "sweep-resume", "sweep-chunks", "tc", "tc-f32acc", "fix", "fields", "tc4", "batch", "rescore",
                              "mlp"],
                     help="run one small case of one kernel (for profilers) and exit")
     ap.add_argument("--case-states", type=int, default=4096)
@@ -127,7 +127,7 @@ class ClockSampler:
             self.buf = open(self.path + ".raw", "w") if self.path else None
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.dev_id, "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -311,13 +311,10 @@ def run_ours(a):
     gE, gidx, _ = global_best(bE, bidx, hX.numpy()[bk], W_, device=dev if world > 1 else None)
 
     pk, pk_kind = peaks()
-    # DRAM bytes (read + write) of one full-size launch of the dense sweep
-    # kernel, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
-    # profiles/sweep_tuned_dense_N256_B4096.md); the kernel is unchanged since.
-    sweep_dram_bytes = 145923840 + 2840064
-    # L2 peak of this GPU as ncu reports it: lts__t_bytes.sum.peak_sustained
-    # (18048 B/cycle) x L2 clock (2.017 GHz), same profile summary.
-    l2_peak_gbs = 18048 * 2.0168e9 / 1e9
+    # L2 read bandwidth of this GPU, measured now: a plain read of a 64 MiB
+    # buffer (fits in L2) from every SM, best of several launches
+    l2 = measure_l2_read_peak(dev)
+    traffic = sweep_traffic_record()
     # sweep kernel: coefficient bytes it read for the accepted flips (counted
     # by the kernel: min(set, clear) rows of the float32 slab of the flipped
     # bit, plus its pair row and column-sum row) and the per-state data it
@@ -338,24 +335,33 @@ def run_ours(a):
                                     "top_count": int(table["count"][0].item()) if table["count"].numel() else 0,
                                     "aggregate_ms": agg_ms},
                    "sweep_kernel_ms": sweep_avg},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": sweep_dram_bytes if a.mode == "tuned" else None,
-                     "kernel": "sweep_tuned_kernel (dense)", "peak_kind": pk_kind,
-                     "note": "coefficient slabs (67 MB) stay in L2: DRAM traffic per launch is ~0.06% of the "
-                             "algorithmic bytes, so the bound that applies is the L2 one below",
-                     "l2": {"achieved": achieved, "peak": l2_peak_gbs, "unit": "GB/s",
-                            "frac": achieved / l2_peak_gbs,
-                            "peak_from": "ncu lts__t_bytes.sum.peak_sustained x L2 clock"}},
+        "roofline": {"bound": "l2", "achieved": achieved, "peak": l2["gbs"], "unit": "GB/s",
+                     "frac": achieved / l2["gbs"],
+                     "traffic": traffic["dram_bytes"] if (a.mode == "tuned" and traffic["current"]) else None,
+                     "kernel": "sweep_tuned_kernel (dense)",
+                     "algorithmic_bytes_per_launch": bytes_sweep,
+                     "peak_kind": "measured in this run: " + l2["how"], "l2_read_gbs_by_buffer_mib": l2["by_size_gbs"],
+                     "traffic_from": traffic["source"],
+                     "note": "the coefficient slabs (67 MB) are read out of L2; traffic is the kernel's DRAM "
+                             "bytes per launch from one ncu capture, null when the kernel sources changed "
+                             "since that capture",
+                     "hbm": {"achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                             "frac_of_algorithmic_bytes": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
+                             "note": "algorithmic bytes over the HBM copy peak; above 1 because they come from L2"}},
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        # per step: initial states, pair pre-pass, tensor-core contraction +
-        # its finalize, sweep, exact re-score (pair part, limb contraction,
+        # per step: initial states, exact tensor-core contraction + its
+        # finalize, sweep, exact re-score (pair part, limb contraction,
         # finalize)
-        "gpu_launches": 8 * a.steps,
+        "gpu_launches": 7 * a.steps,
         "wall_s_timed": wall,
     }
     cl = cs.summary()
     if cl:
         line["clocks"] = cl
+    if rank == 0:
+        # the energy/field contraction of the step (its initial-state call)
+        # at full size, with its tensor-pipe fractions
+        line["contraction"] = measure_dense_contraction(h, inst, B)
     if rank == 0 and not a.no_extras:
         line["time_to_target"] = measure_time_to_target_dense(h, B)
         line["extras"] = {"uneven_batch": measure_uneven_batch(),
@@ -424,6 +430,101 @@ def measure_uneven_batch(plain_sample: int = 8):
             "per_instance_plain_sample": f"first {plain_sample} instances ({sub_flips} flips, {p_ms_sub:.1f} ms)",
             "speedup_graph_vs_plain": (flips / (g_ms / 1000.0)) / p_rate,
             "autotuned_shape": {"warps_per_cta": shape[0], "ctas": shape[1]}}
+
+
+SWEEP_SOURCES = ("paper_2407_19987_gb300/csrc/sweep_impl.cuh", "paper_2407_19987_gb300/csrc/sweep_dense.cu",
+                 "paper_2407_19987_gb300/csrc/hobo_dev.cuh")
+SWEEP_PROFILE = "profiles/sweep_tuned_dense_N256_B4096.md"
+
+
+def sources_sha256(paths=SWEEP_SOURCES) -> str:
+    """SHA-256 over the sources of the dense sweep kernel, in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def sweep_traffic_record(profile: str = SWEEP_PROFILE) -> dict:
+    """The DRAM bytes of one full-size sweep launch from the profile
+    summary's `traffic_record:` line (kernel sources hash, bytes), and
+    whether the sources still hash the same."""
+    out = {"dram_bytes": None, "current": False, "source": profile}
+    try:
+        with open(os.path.join(ROOT, profile)) as f:
+            for line in f:
+                if line.startswith("traffic_record:"):
+                    kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+                    out["dram_bytes"] = int(kv["dram_bytes_per_launch"])
+                    out["current"] = kv.get("sources_sha256") == sources_sha256()
+                    out["source"] = f"{profile} (sources {'unchanged' if out['current'] else 'changed'} since the capture)"
+    except (OSError, KeyError, ValueError):
+        pass
+    return out
+
+
+def measure_l2_read_peak(dev, sizes_mib=(8, 16, 32, 48, 64), launches: int = 10) -> dict:
+    """Read bandwidth out of L2: hobo_probe_l2_read over buffers of several
+    sizes that fit in L2 (each launch reads its buffer repeatedly, about
+    2.5 GB per launch), best CUDA-event time of `launches` launches after a
+    warm-up; the peak is the best size's."""
+    import torch
+
+    import paper_2407_19987_gb300 as H
+    per = {}
+    for mib in sizes_mib:
+        buf = torch.ones(mib * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        reps = max(1, 2560 // mib)
+        H.probe_l2_read(buf, reps)
+        ms = min(_timed_ms(lambda: H.probe_l2_read(buf, reps))[1] for _ in range(launches))
+        per[mib] = buf.numel() * 4 * reps / (ms / 1000.0) / 1e9
+        del buf
+    best = max(per, key=per.get)
+    return {"gbs": per[best],
+            "how": f"hobo_probe_l2_read (16-byte L2-only loads from every SM), best of buffers "
+                   f"{list(sizes_mib)} MiB: {best} MiB, best of {launches} launches",
+            "by_size_gbs": {str(k): round(v, 1) for k, v in per.items()}}
+
+
+def measure_dense_contraction(h, inst, B: int, reps: int = 5) -> dict:
+    """Energies and all N flip deltas of B random states of the dense
+    workload in one hobo_energy call: the exact tensor-core path (limb
+    planes of the upper-triangular slabs) and, for comparison, the
+    float32-accumulating tensor-core kernel (three bf16 planes of the full
+    slabs).  Algorithmic flops per state: 2 per cubic monomial for the
+    energy and 2 per cubic monomial for each of its three fields,
+    8 * C(N, 3) (pairs add O(N^2)); issued: 2 * 128 * K * (columns) per
+    MMA, summed over the kernel's MMAs."""
+    import torch
+
+    import paper_2407_19987_gb300 as H
+    N = inst.N
+    X = torch.from_numpy(W.pack_bits(W.random_states(9, B, N)).view(np.int32)).cuda()
+    info = h.info()
+    pk, pk_kind = peaks()
+    m3 = N * (N - 1) * (N - 2) // 6
+    alg = 8.0 * m3 * B
+    tiles = -(-B // 128)
+    KP = -(-N // 64) * 64
+    nkb = KP // 64
+    out = {"workload": f"dense order 3, N={N}, {B} random states, energies and all flip deltas",
+           "algorithmic_flops": alg, "peak_tflops": pk["bf16_tflops"], "peak_kind": pk_kind}
+    for name, path in (("exact", H.PATH_TENSOR_CORE), ("f32acc", H.PATH_TENSOR_CORE_F32ACC)):
+        h.energy(X, path=path)
+        ms = float(np.median([_timed_ms(lambda: h.energy(X, path=path))[1] for _ in range(reps)]))
+        if name == "exact":
+            L = info["tc_limbs"]
+            issued = 2.0 * tiles * 128 * N * L * sum(64 * (kb + 1) * 64 for kb in range(nkb))
+        else:
+            NJ = -(-N // 16) * 16
+            issued = 2.0 * tiles * 128 * N * 3 * NJ * KP
+        out[name] = {"ms": ms, "algorithmic_tflops": alg / (ms / 1e3) / 1e12,
+                     "algorithmic_frac": alg / (ms / 1e3) / 1e12 / pk["bf16_tflops"],
+                     "issued_tflops": issued / (ms / 1e3) / 1e12,
+                     "issued_frac": issued / (ms / 1e3) / 1e12 / pk["bf16_tflops"]}
+    return out
 
 
 def _timed_ms(fn):
@@ -704,7 +805,7 @@ def run_kernel_case(a):
     """One small case of one kernel, for profilers.  Dense workload: sweep:
     an anneal of --case-states states over --case-sweeps sweeps of the
     schedule from --case-offset; sweep-resume: sweeps [0, --case-offset)
-    and then, resumed, --case-sweeps more (profile the second launch); tc: two tensor-core contractions of 4096
+    and then, resumed, --case-sweeps more (profile the second launch); tc / tc-f32acc: two exact / float32-accumulating tensor-core contractions of 4096
     random states; fix: two exact re-scores of 4096 random states on CUDA
     cores; rescore: the same on the tensor cores (limb planes).  fields:
     two term-list energy+field contractions of 4096 random states of the
@@ -779,6 +880,8 @@ def run_kernel_case(a):
         for _ in range(2):
             if a.kernel_case == "tc":
                 h.energy(X, path=H.PATH_TENSOR_CORE)
+            elif a.kernel_case == "tc-f32acc":
+                h.energy(X, path=H.PATH_TENSOR_CORE_F32ACC)
             else:
                 h.energy_fp64(X)
     torch.cuda.synchronize()

@@ -108,6 +108,9 @@ typedef struct {
                               sum |c| < 2^24 (bit-exact float32 path) */
     int64_t terms[HOBO_MAX_ORDER + 1];  /* folded monomials per degree */
     double abs_sum;        /* sum of |folded coefficient| */
+    int tc_limbs;          /* dense order-3 instances: 8-bit limbs per
+                              fixed-point coefficient in the exact
+                              tensor-core contraction (0 = not built) */
 } hobo_info_t;
 
 int hobo_info(hobo_h h, hobo_info_t* info);
@@ -120,18 +123,29 @@ int hobo_info(hobo_h h, hobo_info_t* info);
  *   X   device uint32 [B][W] packed states
  *   E   device float32 [B]
  *   dE  device float32 [B][N], or NULL to skip the flip deltas
- * Dense order-3 instances run the tcgen05 tensor-core contraction
- * (tensor reshaped to (N^2 x N) against the bit matrix, bf16 split of the
- * coefficients, float32 accumulation); others the term-list kernel.
- * Integer instances give exact results.  B >= 0 (B = 0 is a no-op).
- * Errors: HOBO_ERR_ARG, HOBO_ERR_CUDA.
+ * Dense order-3 instances (N <= 256) run the tcgen05 tensor-core
+ * contraction: the tensor reshaped to (N^2 x N) rows (m, j) against the bit
+ * matrix, upper triangle j < l of each slab only, on exact 8-bit limbs of
+ * the fixed-point coefficients round(c * 2^S), integer sums, one rounding
+ * to float32 (energies only: the re-score's m < j < l limbs).  Dense
+ * order-4 instances with N <= 64 run the order-4 tensor-core contraction
+ * (bf16 split, float32 accumulation); others the term-list kernel (exact
+ * 64-bit fixed-point sums, one rounding).  Integer instances give exact
+ * results on every path; the exact paths give identical floats.
+ * B >= 0 (B = 0 is a no-op).  Errors: HOBO_ERR_ARG, HOBO_ERR_CUDA.
  */
 int hobo_energy(hobo_h h, const uint32_t* X, int B, float* E, float* dE, void* stream);
 
 /* hobo_energy with an explicit contraction path:
- *   path 0 = automatic, 1 = term-list kernel (CUDA cores, float32),
- *   path 2 = tcgen05 tensor-core kernel (dense order-3 instances only;
- *            HOBO_ERR_UNSUPPORTED otherwise). */
+ *   path 0 = automatic, 1 = term-list kernel (CUDA cores, exact fixed point),
+ *   path 2 = tcgen05 tensor-core kernel (dense order-3 instances: exact
+ *            fixed-point limbs; dense order-4: bf16 split, float32 sums;
+ *            HOBO_ERR_UNSUPPORTED otherwise),
+ *   path 3 = tcgen05 kernel of dense order-3 instances on bf16 split
+ *            planes of the full slabs with float32 accumulation (the
+ *            Sec. IV.C contraction in plain tensor-core precision; float
+ *            instances then carry float32 summation error; kept for
+ *            comparison; HOBO_ERR_UNSUPPORTED otherwise). */
 int hobo_energy_path(hobo_h h, const uint32_t* X, int B, float* E, float* dE, int path,
                      void* stream);
 
@@ -246,6 +260,34 @@ int hobo_check(hobo_h h, void* stream);
  * Errors: HOBO_ERR_ARG (NULL h, limit out of range), HOBO_ERR_CUDA.
  */
 int hobo_selftest_timeout(hobo_h h, uint64_t limit_ns, void* stream);
+
+/*
+ * hobo_selftest_philox -- diagnostic of the random stream (no counterpart in
+ * the paper; the generator is Philox4x32-10 of Salmon et al., SC'11): for
+ * each of n inputs, counter ctr[4i..4i+3] and key key[2i..2i+1] (device
+ * arrays), writes the library's Philox4x32-10 block to ours[4i..4i+3] and
+ * that of the CUDA toolkit's cuRAND device header (curand_Philox4x32_10) to
+ * ref[4i..4i+3] (device arrays the caller owns).  The two must agree bit for
+ * bit.  Errors: HOBO_ERR_ARG (n < 0, NULL array), HOBO_ERR_CUDA.
+ */
+int hobo_selftest_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* ours, uint32_t* ref,
+                         void* stream);
+
+/*
+ * hobo_probe_l2_read -- measurement kernel with no counterpart in the paper:
+ * enqueues on `stream` one launch that reads the device buffer `buf`
+ * (`bytes` bytes, 16-byte aligned, a multiple of 16, at least 4096) `reps`
+ * times in 16-byte loads cached in L2 only, from every SM (consecutive
+ * threads read consecutive vectors; each thread steps through the buffer
+ * with a stride of the grid's thread count, wrapping around).  With a
+ * buffer that fits in L2 the caller's CUDA-event time of the launch gives
+ * the GPU's L2-to-SM read bandwidth, bytes * reps / time: the denominator
+ * of the sweep kernel's L2 roofline, since the sweep reads its coefficient
+ * slabs out of L2.  Reads
+ * only; writes nothing the caller sees.  Errors: HOBO_ERR_ARG (alignment,
+ * size, reps outside 1..4096), HOBO_ERR_CUDA.
+ */
+int hobo_probe_l2_read(const void* buf, int64_t bytes, int reps, void* stream);
 
 /* ---- batches of instances ---------------------------------------------- */
 

@@ -34,7 +34,7 @@ HOBO_RESCORE_CUDA_CORES = 32
 HOBO_ANNEAL_TUNED = 0
 HOBO_ANNEAL_PLAIN = 1
 
-PATH_AUTO, PATH_TERMS, PATH_TENSOR_CORE = 0, 1, 2
+PATH_AUTO, PATH_TERMS, PATH_TENSOR_CORE, PATH_TENSOR_CORE_F32ACC = 0, 1, 2, 3
 
 HOBO_MAX_ORDER = 8
 HOBO_NOALLOC_MAX_B = 65536
@@ -49,7 +49,7 @@ class HoboError(RuntimeError):
 class hobo_info_t(C.Structure):
     _fields_ = [("N", C.c_int), ("order", C.c_int), ("words", C.c_int), ("dense", C.c_int),
                 ("integer", C.c_int), ("terms", C.c_int64 * (HOBO_MAX_ORDER + 1)),
-                ("abs_sum", C.c_double)]
+                ("abs_sum", C.c_double), ("tc_limbs", C.c_int)]
 
 
 HOBO_BATCH_GRAPH = 0
@@ -110,6 +110,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     L.hobo_aggregate.restype = I
     L.hobo_selftest_timeout.argtypes = [P, U64, P]
     L.hobo_selftest_timeout.restype = I
+    L.hobo_selftest_philox.argtypes = [P, P, I64, P, P, P]
+    L.hobo_selftest_philox.restype = I
+    L.hobo_probe_l2_read.argtypes = [P, I64, I, P]
+    L.hobo_probe_l2_read.restype = I
     L.hobo_energy_fp64_noalloc.argtypes = [P, P, I, P, P]
     L.hobo_energy_fp64_noalloc.restype = I
     L.hobo_batch_create.argtypes = [C.POINTER(P), P, I, P]
@@ -216,7 +220,8 @@ class Instance:
         inf = hobo_info_t()
         _check(load_library().hobo_info(self._h, C.byref(inf)))
         return dict(N=inf.N, order=inf.order, words=inf.words, dense=bool(inf.dense),
-                    integer=bool(inf.integer), terms=list(inf.terms), abs_sum=inf.abs_sum)
+                    integer=bool(inf.integer), terms=list(inf.terms), abs_sum=inf.abs_sum,
+                    tc_limbs=inf.tc_limbs)
 
     def energy(self, X, with_delta: bool = True, path: int = PATH_AUTO, stream=None):
         """X: int32 CUDA tensor [B, W] of packed states.  Returns (E [B] f32,
@@ -551,3 +556,21 @@ def aggregate(X, E, stream=None) -> dict:
                                          _ptr(K), _stream(stream)))
     k = int(K.item())
     return {"states": U[:k], "energy": UE[:k], "count": cnt[:k], "first": first[:k]}
+
+
+def selftest_philox(ctr, key, stream=None):
+    """hobo_selftest_philox: the library's Philox4x32-10 blocks and those of
+    the cuRAND device header for counters ctr (uint32 CUDA [n, 4], as int32)
+    and keys key ([n, 2]).  Returns (ours, ref), int32 CUDA [n, 4]."""
+    import torch
+    n = ctr.shape[0]
+    ours = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
+    ref = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
+    _check(load_library().hobo_selftest_philox(_ptr(ctr), _ptr(key), n, _ptr(ours), _ptr(ref), _stream(stream)))
+    return ours, ref
+
+
+def probe_l2_read(buf, reps: int, stream=None):
+    """hobo_probe_l2_read: one launch reading the CUDA buffer `buf` reps
+    times (16-byte loads cached in L2 only); time it with CUDA events."""
+    _check(load_library().hobo_probe_l2_read(_ptr(buf), buf.numel() * buf.element_size(), reps, _stream(stream)))

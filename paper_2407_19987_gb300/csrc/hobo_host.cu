@@ -94,7 +94,7 @@ static void free_layouts(DevLayouts& d)
 {
     void* ptrs[] = {d.tvars, d.tfix, d.fptr, d.fvars, d.ffix, d.cptr, d.chdr,
                     d.ltgt, d.lcnt, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf, d.S3limb, d.rs_a, d.rs_S2,
-                    d.C3fix, d.S2fix, d.afix, d.pair_m, d.pair_j, d.S4bf};
+                    d.C3fix, d.S2fix, d.afix, d.pair_m, d.pair_j, d.S4bf, d.S3flimb, d.fa};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DevLayouts{};
@@ -177,6 +177,63 @@ static int build_exact_limbs(hobo_instance* h, const std::vector<Entry>& mono)
     if (make_tc_tensor_map_rs(h) != cudaSuccess) {
         (void)cudaGetLastError();
         d.tmap_rs_ok = false;
+    }
+    return HOBO_OK;
+}
+
+// Limb planes of the fixed-point coefficients for the exact energy/field
+// contraction on the tensor cores (layout in DevLayouts): each cubic
+// monomial {v0 < v1 < v2} goes to the slab of each of its members m, at row
+// j and column l > j of the other two; each pair {m, j} to the diagonal
+// (j, j) of m's slab and (m, m) of j's.  The scale keeps the sum of all |C|
+// below 2^62, so every field and energy sum fits in 64 bits and at most 8
+// limbs are needed.
+static int build_field_limbs(hobo_instance* h, const std::vector<Entry>& mono)
+{
+    DevLayouts& d = h->d;
+    const int N = h->N;
+    const int S = h->integer ? 0 : d.fix_shift;
+    long long maxC = 0;
+    for (auto& e : mono) {
+        const long long f = std::llrint(std::ldexp(e.c, S));
+        if (e.m.d >= 2) maxC = std::max(maxC, f < 0 ? -f : f);
+    }
+    int L = 1;
+    while (L < 8 && maxC >= (1LL << (8 * L - 1))) ++L;
+    const int KP = d.KP;
+    const size_t plane = (size_t)N * KP * KP;
+    std::vector<uint16_t> limbs(plane * L, 0);
+    std::vector<long long> fa((size_t)N, 0);
+    auto put = [&](size_t at, long long f) {
+        const uint64_t u = (uint64_t)f;
+        for (int q = 0; q < L; ++q) {
+            int limb = (int)((u >> (8 * q)) & 0xFFu);
+            if (q == L - 1 && limb >= 128) limb -= 256;     // signed top limb
+            limbs[q * plane + at] = bf16_of_small_int(limb);
+        }
+    };
+    for (auto& e : mono) {
+        const long long f = std::llrint(std::ldexp(e.c, S));
+        if (e.m.d == 1) {
+            fa[e.m.v[0]] = f;
+        } else if (e.m.d == 2) {
+            const int m = e.m.v[0], j = e.m.v[1];
+            put(((size_t)m * KP + j) * KP + j, f);
+            put(((size_t)j * KP + m) * KP + m, f);
+        } else {
+            const int v[3] = {e.m.v[0], e.m.v[1], e.m.v[2]};
+            // (m, j, l): each member as m, the other two ascending
+            const int at3[3][3] = {{v[0], v[1], v[2]}, {v[1], v[0], v[2]}, {v[2], v[0], v[1]}};
+            for (auto& t : at3) put(((size_t)t[0] * KP + t[1]) * KP + t[2], f);
+        }
+    }
+    int rc;
+    if ((rc = upload(&d.S3flimb, limbs)) || (rc = upload(&d.fa, fa))) return rc;
+    d.fl_L = L;
+    d.fl_shift = S;
+    if (make_tc_tensor_map_fl(h) != cudaSuccess) {
+        (void)cudaGetLastError();
+        d.tmap_fl_ok = false;
     }
     return HOBO_OK;
 }
@@ -412,6 +469,7 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
                 d.tmap_ok = false;
             }
             if (!(flags & HOBO_RESCORE_CUDA_CORES) && (rc = build_exact_limbs(h, mono))) return rc;
+            if ((rc = build_field_limbs(h, mono))) return rc;
         }
     } else {
         // order-4 tensor-core contraction when the quartic part is dense
@@ -580,8 +638,26 @@ int hobo::energy_dispatch(const hobo_instance* h, const uint32_t* X, int B, floa
         if (e == cudaSuccess) return HOBO_OK;
         return cuda_fail(e, "order-4 tensor-core contraction");
     }
-    if (path == 2 || (path == 0 && h->dense)) {
+    if (path == 3) {
         cudaError_t e = launch_energy_tc(h, X, B, E, g, flip, st);
+        if (e == cudaSuccess) return HOBO_OK;
+        if (e != cudaErrorNotSupported) return cuda_fail(e, "tensor-core contraction");
+        (void)cudaGetLastError();
+        return fail(HOBO_ERR_UNSUPPORTED, "float32-accumulating tensor-core path needs a dense order-3 instance");
+    }
+    if (path == 2 || (path == 0 && h->dense)) {
+        // exact fixed point on the tensor cores: energies only from the
+        // re-score planes, energies and fields from the field planes; the
+        // float32-accumulating kernel where neither exists
+        cudaError_t e = !g ? launch_energy_exact_f32(h, X, B, E, st) : launch_energy_tc_fix(h, X, B, E, g, flip, st);
+        if (e == cudaErrorNotSupported) {
+            (void)cudaGetLastError();
+            e = launch_energy_tc_fix(h, X, B, E, g, flip, st);
+        }
+        if (e == cudaErrorNotSupported) {
+            (void)cudaGetLastError();
+            e = launch_energy_tc(h, X, B, E, g, flip, st);
+        }
         if (e == cudaSuccess) return HOBO_OK;
         if (e != cudaErrorNotSupported) return cuda_fail(e, "tensor-core contraction");
         if (path == 2)
@@ -702,6 +778,7 @@ int hobo_info(hobo_h h, hobo_info_t* info)
     info->integer = h->integer ? 1 : 0;
     for (int q = 0; q <= HOBO_MAX_ORDER; ++q) info->terms[q] = h->terms[q];
     info->abs_sum = h->abs_sum;
+    info->tc_limbs = h->d.S3flimb ? h->d.fl_L : 0;
     return HOBO_OK;
 }
 
@@ -709,7 +786,7 @@ int hobo_energy_path(hobo_h h, const uint32_t* X, int B, float* E, float* dE, in
 {
     if (!h) return fail(HOBO_ERR_ARG, "NULL instance");
     if (B < 0 || (B > 0 && (!X || !E))) return fail(HOBO_ERR_ARG, "bad X/E/B");
-    if (path < 0 || path > 2) return fail(HOBO_ERR_ARG, "path must be 0, 1 or 2");
+    if (path < 0 || path > 3) return fail(HOBO_ERR_ARG, "path must be 0, 1, 2 or 3");
     if (B == 0) return HOBO_OK;
     return hobo::energy_dispatch(h, X, B, E, dE, true, path, (cudaStream_t)stream);
 }

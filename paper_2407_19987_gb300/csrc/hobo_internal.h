@@ -79,6 +79,20 @@ struct DevLayouts {
     int rs_L = 0, rs_shift = 0;
     alignas(64) unsigned char tmap_rs[128] = {};
     bool tmap_rs_ok = false;
+    // exact energies and fields on the tensor cores (N <= 256): the
+    // fixed-point coefficients C = round(c * 2^fl_shift) of every monomial
+    // containing m in m's slab, a cubic {m, j, l} at row j, column l > j
+    // (the upper triangle), a pair {m, j} on the diagonal (j, j) (rows and
+    // columns = m hold zeros), as fl_L limbs in exact bf16 planes
+    // [fl_L][N][KP][KP] (rows padded to KP = N rounded up to 64); linear
+    // coefficients fa[N] at the same scale.  fl_shift = 0 for integer
+    // instances, fix_shift otherwise, so results equal the term-list
+    // path's.
+    uint16_t* S3flimb = nullptr;
+    long long* fa = nullptr;
+    int fl_L = 0, fl_shift = 0;
+    alignas(64) unsigned char tmap_fl[128] = {};
+    bool tmap_fl_ok = false;
     // order-4 tensor-core contraction (order-4 instances, N <= 64, quartic
     // part dense): the symmetric quartic tensor as bf16 split planes
     // [nsplit4][N][R4][64], row (j, k) = j * 64 + k (k >= N zero), R4 = (N
@@ -146,6 +160,13 @@ cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, f
                              float* g_or_dE, bool flip_out, cudaStream_t st);
 bool tc_supported(const hobo_instance* h);
 bool exact_tc_supported(const hobo_instance* h);
+bool fix_tc_supported(const hobo_instance* h);
+cudaError_t make_tc_tensor_map_fl(hobo_instance* h);
+// exact fixed-point energies and fields on the tensor cores (limb planes of
+// the upper-triangular slabs), rounded once to float32
+cudaError_t launch_energy_exact_f32(const hobo_instance* h, const uint32_t* X, int B, float* E, cudaStream_t st);
+cudaError_t launch_energy_tc_fix(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g_or_dE,
+                                 bool flip_out, cudaStream_t st);
 cudaError_t launch_wait_timeout_selftest(const hobo_instance* h, uint64_t limit_ns, cudaStream_t st);
 cudaError_t make_tc_tensor_map(hobo_instance* h);
 cudaError_t make_tc_tensor_map_rs(hobo_instance* h);
@@ -188,7 +209,8 @@ int guarded(const char* what, F&& body)
 }
 
 // Energy/field contraction with the automatic or explicit path (0 auto,
-// 1 term list, 2 tensor core); returns a HOBO_* status.
+// 1 term list, 2 tensor core exact, 3 tensor core with float32
+// accumulation); returns a HOBO_* status.
 int energy_dispatch(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g, bool flip,
                     int path, cudaStream_t st);
 

@@ -241,6 +241,26 @@ cudaError_t launch_energy_terms(const hobo_instance* h, const uint32_t* X, int B
     return e;
 }
 
+// Energies only of a dense instance, exact on the tensor cores (the
+// re-score's limb planes, m < j < l), rounded once to float32 like the
+// term-list path; cudaErrorNotSupported without those planes.
+cudaError_t launch_energy_exact_f32(const hobo_instance* h, const uint32_t* X, int B, float* E, cudaStream_t st)
+{
+    if (!exact_tc_supported(h)) return cudaErrorNotSupported;
+    if (B == 0) return cudaSuccess;
+    unsigned long long* acc = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&acc, sizeof(unsigned long long) * (size_t)B, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)B, st);
+    if (e == cudaSuccess) e = launch_energy_exact_tc(h, X, B, acc, st);
+    if (e == cudaSuccess) {
+        energy_fix_finalize_f32<<<(B + 255) / 256, 256, 0, st>>>(acc, B, h->d.rs_shift, E);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(acc, st);
+    return e;
+}
+
 // ===========================================================================
 // float64 re-scoring: the same exact fixed-point energies, rounded once to
 // float64 (integer instances exact; otherwise the error is at most

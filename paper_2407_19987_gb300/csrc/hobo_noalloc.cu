@@ -16,7 +16,6 @@
 // streams, without ordering between them) race on the array and give wrong
 // results; callers must order them, for example by issuing them on one
 // stream.
-#include <mutex>
 #include <string>
 #include "hobo_internal.h"
 
@@ -27,26 +26,19 @@ constexpr int kNoAllocMaxStates = HOBO_NOALLOC_MAX_B;
 
 static __device__ __align__(256) unsigned long long g_fix_scratch[kNoAllocMaxStates];
 
-// Device address of g_fix_scratch per device.  In host code the symbol is
-// only a stand-in and must never be passed to a kernel; the address is looked
-// up once per device, with that device current, on the first call there.
-static std::mutex g_scratch_mu;
-static void* g_scratch_ptr[64] = {};
-
+// Device address of g_fix_scratch on the current device.  In host code the
+// symbol is only a stand-in and must never be passed to a kernel.  The
+// address is looked up on every call, with the call's device current: after
+// the first lookup on a device (which may load the library's device code
+// there, so make that first call before any stream capture) it is a cheap
+// host-side query, and no address is kept that a device reset could leave
+// stale.
 static cudaError_t scratch_for_current_device(void** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_fix_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_fix_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -54,7 +46,7 @@ static cudaError_t scratch_for_current_device(void** out)
 
 using namespace hobo;
 
-extern "C" int hobo_energy_fp64_noalloc(hobo_h h, const uint32_t* X, int B, double* E, void* stream)
+static int hobo_energy_fp64_noalloc_impl(hobo_h h, const uint32_t* X, int B, double* E, void* stream)
 {
     if (!h) { set_error("NULL instance"); return HOBO_ERR_ARG; }
     if (B < 0 || (B > 0 && (!X || !E))) { set_error("bad X/E/B"); return HOBO_ERR_ARG; }
@@ -82,4 +74,14 @@ extern "C" int hobo_energy_fp64_noalloc(hobo_h h, const uint32_t* X, int B, doub
     }
     set_error("");
     return HOBO_OK;
+}
+
+// Under the same guard as the other entry points: the error messages build
+// host strings, and the exact re-score's launcher a small host vector, so a
+// failed host allocation becomes HOBO_ERR_OOM instead of an exception
+// crossing the C ABI.
+extern "C" int hobo_energy_fp64_noalloc(hobo_h h, const uint32_t* X, int B, double* E, void* stream)
+{
+    return hobo::guarded("hobo_energy_fp64_noalloc",
+                         [&] { return hobo_energy_fp64_noalloc_impl(h, X, B, E, stream); });
 }

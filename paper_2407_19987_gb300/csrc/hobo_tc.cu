@@ -1078,6 +1078,345 @@ cudaError_t launch_energy_exact_tc(const hobo_instance* h, const uint32_t* X, in
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Exact energies and fields on the tensor cores.  The fixed-point
+// coefficients C = round(c * 2^S) of every monomial containing m sit in m's
+// slab: a cubic {m, j, l} at row j, column l > j (the upper triangle), a
+// pair {m, j} on the diagonal (j, j); each plane holds one 8-bit limb of
+// them (exact bf16).  For a tile of 128 states and an item (m, limb q) the
+// tensor cores form
+//   D_q[b][j] = sum_{l >= j} limb_q[m][j][l] x_bl
+// whose products are integers of magnitude <= 255 and whose sums stay below
+// 2^24, so they are exact in float32, and so are the epilogue's sums over
+// the set bits j of the state below and above m,
+//   u_q = sum_{j < m} x_bj D_q[b][j],   t_q = sum_{j > m} x_bj D_q[b][j].
+// With t = sum_q t_q 2^(8q) and s = t + sum_q u_q 2^(8q) (64-bit integers):
+//   g_bm = a_m + s   (the field: every pair and cubic term containing m),
+//   E_b  = sum_m x_bm (a_m + t)   (t: the terms whose smallest member is m),
+// each rounded once to float32 -- the term-list path's values, bit for bit.
+// Only the triangle is fed to the tensor cores: K block kb (l in
+// [64 kb, 64 kb + 64)) meets rows j < 64 (kb + 1), so its MMAs run with
+// N = 64 (kb + 1) columns, largest first (that one clears the accumulator):
+// 10/16 of the full slab for N = 256.
+// ---------------------------------------------------------------------------
+struct TcFixParams {
+    const uint32_t* X;
+    int B, N, W, KP, L, S;
+    int T, chunks, G;
+    const long long* fa;     // [N]
+    float* out_g;
+    int flip;
+    unsigned long long* Epart;   // [G][128]: this chunk's part of the fixed-point energy (mod 2^64)
+    int* status;
+};
+
+// Adds the accumulator columns whose bit is set in xw into four partial
+// sums (exact: integers below 2^24).
+__device__ __forceinline__ void add_set_columns(const uint32_t (&v)[32], uint32_t xw, float (&c)[4])
+{
+#pragma unroll
+    for (int t = 0; t < 32; t += 4) {
+        if ((xw >> t) & 1u) c[0] = __fadd_rn(c[0], __uint_as_float(v[t]));
+        if ((xw >> (t + 1)) & 1u) c[1] = __fadd_rn(c[1], __uint_as_float(v[t + 1]));
+        if ((xw >> (t + 2)) & 1u) c[2] = __fadd_rn(c[2], __uint_as_float(v[t + 2]));
+        if ((xw >> (t + 3)) & 1u) c[3] = __fadd_rn(c[3], __uint_as_float(v[t + 3]));
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+energy_tc_fix_kernel(const __grid_constant__ CUtensorMap tmap, const TcFixParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int nKB = p.KP / kTcKB;
+    const uint32_t stage_bytes = (uint32_t)p.KP * 128u;
+    uint8_t* sA = smem;
+    uint8_t* sB = sA + nKB * 16384;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kTcStages * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kTcStages;
+    uint64_t* afull = bars + 2 * kTcStages;
+    uint64_t* aempty = afull + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(aempty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+    volatile int* never_set = abort_flag + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = p.N, W = p.W, B = p.B;
+    const int c = blockIdx.x;
+    const int tile_c = c % p.T, chunk = c / p.T;
+    const int i0 = tile_c * N + (int)((int64_t)chunk * N / p.chunks);
+    const int i1 = tile_c * N + (int)((int64_t)(chunk + 1) * N / p.chunks);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&afull[s], 1);
+            mbar_init(&aempty[s], 4);
+        }
+        *abort_flag = 0;
+        *never_set = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    int pstage = 0;
+    uint32_t pphase = 0;
+    uint32_t armed_phase[kTcStages];
+    bool armed[kTcStages];
+    for (int s = 0; s < kTcStages; ++s) { armed[s] = false; armed_phase[s] = 0; }
+    int cstage = 0;
+    uint32_t cphase = 0;
+    int acc_mma = 0, acc_epi = 0;
+
+    for (int it = i0; it < i1;) {
+        const int tile = it / N;
+        const int seg_end = min(i1, (tile + 1) * N);
+        {
+            const int cpr = p.KP / 8;
+            for (int q = threadIdx.x; q < kTcM * cpr; q += blockDim.x) {
+                const int r = q / cpr, cc = q % cpr;
+                const int kb = cc >> 3, ch = cc & 7;
+                const int b = tile * kTcM + r;
+                const int l0 = cc * 8;
+                uint32_t byte = 0;
+                if (b < B && l0 < N) {
+                    byte = (p.X[(int64_t)b * W + (l0 >> 5)] >> (l0 & 31)) & 0xFFu;
+                    const int rem = N - l0;
+                    if (rem < 8) byte &= (1u << rem) - 1u;
+                }
+                uint32_t wv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t lo = ((byte >> (2 * e)) & 1u) ? 0x3F80u : 0u;
+                    const uint32_t hi = ((byte >> (2 * e + 1)) & 1u) ? 0x3F80u : 0u;
+                    wv[e] = lo | (hi << 16);
+                }
+                uint8_t* dst = sA + kb * 16384 + (r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4);
+                *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+
+        if (warp == 0) {
+            if (lane == 0) {
+                // ---- producer: rows j < 64 (kb + 1) of K block kb, kb descending
+                bool ok = true;
+                for (int j = it; j < seg_end && ok && !*abort_flag; ++j) {
+                    const int m = j % N;
+                    for (int q = 0; q < p.L && ok; ++q)
+                        for (int kb = nKB - 1; kb >= 0; --kb) {
+                            if (!mbar_wait(&empty[pstage], pphase ^ 1u, abort_flag)) {
+                                set_abort(abort_flag, p.status);
+                                ok = false;
+                                break;
+                            }
+                            mbar_expect_tx(&full[pstage], (uint32_t)(kb + 1) * 64u * 128u);
+                            for (int rb = 0; rb <= kb; ++rb)
+                                tma_load_2d(sB + pstage * stage_bytes + rb * 8192, &tmap, kb * kTcKB,
+                                            (q * N + m) * p.KP + rb * 64, &full[pstage]);
+                            armed[pstage] = true;
+                            armed_phase[pstage] = pphase;
+                            if (++pstage == kTcStages) { pstage = 0; pphase ^= 1u; }
+                        }
+                }
+            }
+        } else if (warp == 1) {
+            if (lane == 0) {
+                // ---- MMA issuer: one accumulator per item (m, q)
+                bool ok = true;
+                for (int j = it; j < seg_end && ok && !*abort_flag; ++j) {
+                    for (int q = 0; q < p.L && ok; ++q) {
+                        const int buf = acc_mma & 1;
+                        if (!mbar_wait(&aempty[buf], (((uint32_t)acc_mma >> 1) & 1u) ^ 1u, abort_flag)) {
+                            set_abort(abort_flag, p.status);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d = tmem + (uint32_t)(buf * 256);
+                        uint32_t accum = 0;
+                        for (int kb = nKB - 1; kb >= 0; --kb) {
+                            if (!mbar_wait(&full[cstage], cphase, abort_flag)) {
+                                set_abort(abort_flag, p.status);
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t idesc = idesc_bf16(kTcM, 64 * (kb + 1));
+                            const uint32_t a0 = smem_u32(sA + kb * 16384);
+                            const uint32_t b0 = smem_u32(sB + cstage * stage_bytes);
+#pragma unroll
+                            for (int k = 0; k < kTcKB / 16; ++k) {
+                                tc_mma(d, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), idesc, accum);
+                                accum = 1;
+                            }
+                            tc_commit(&empty[cstage]);
+                            if (++cstage == kTcStages) { cstage = 0; cphase ^= 1u; }
+                        }
+                        if (!ok) break;
+                        tc_commit(&afull[buf]);
+                        ++acc_mma;
+                    }
+                }
+            }
+        } else {
+            // ---- epilogue: thread = TMEM lane = state row
+            const int quad = warp & 3;
+            const int r = quad * 32 + lane;
+            const int b = tile * kTcM + r;
+            uint32_t x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                uint32_t v = (b < B && k < W) ? p.X[(int64_t)b * W + k] : 0u;
+                const int rem = N - 32 * k;
+                if (rem <= 0) v = 0u; else if (rem < 32) v &= (1u << rem) - 1u;
+                x[k] = v;
+            }
+            unsigned long long esum = 0;
+            const int nch = (N + 31) / 32;
+            bool ok = true;
+            for (int j = it; j < seg_end && ok; ++j) {
+                const int m = j % N;
+                const int mch = m >> 5;
+                // bits of the chunk holding m: above m / below m
+                const uint32_t above_m = (m & 31) == 31 ? 0u : (0xFFFFFFFFu << ((m & 31) + 1));
+                unsigned long long sf = 0, tf = 0;
+                for (int q = 0; q < p.L; ++q) {
+                    const int buf = acc_epi & 1;
+                    ok = __all_sync(0xffffffffu, mbar_wait(&afull[buf], ((uint32_t)acc_epi >> 1) & 1u, abort_flag));
+                    if (!ok) {
+                        if (lane == 0) set_abort(abort_flag, p.status);
+                        break;
+                    }
+                    tc_fence_after();
+                    float lo[4] = {0.f, 0.f, 0.f, 0.f}, hi[4] = {0.f, 0.f, 0.f, 0.f};
+                    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256);
+#pragma unroll 1
+                    for (int ch = 0; ch < nch; ++ch) {
+                        uint32_t v[32];
+                        tmem_ld32(tbase + (uint32_t)(ch * 32), v);
+                        tmem_ld_wait();
+                        uint32_t xw = x[0];
+#pragma unroll
+                        for (int k = 1; k < 8; ++k) xw = (ch == k) ? x[k] : xw;
+                        if (ch < mch) {
+                            add_set_columns(v, xw, lo);
+                        } else if (ch > mch) {
+                            add_set_columns(v, xw, hi);
+                        } else {
+                            add_set_columns(v, xw & ~above_m, lo);
+                            add_set_columns(v, xw & above_m, hi);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&aempty[buf]);
+                    ++acc_epi;
+                    const long long uq = __float2ll_rn(__fadd_rn(__fadd_rn(lo[0], lo[1]), __fadd_rn(lo[2], lo[3])));
+                    const long long tq = __float2ll_rn(__fadd_rn(__fadd_rn(hi[0], hi[1]), __fadd_rn(hi[2], hi[3])));
+                    tf += (unsigned long long)tq << (8 * q);
+                    sf += (unsigned long long)(uq + tq) << (8 * q);
+                }
+                if (!ok) break;
+                const unsigned long long am = (unsigned long long)__ldg(p.fa + m);
+                uint32_t xmw = x[0];
+#pragma unroll
+                for (int k = 1; k < 8; ++k) xmw = (mch == k) ? x[k] : xmw;
+                const bool xm = (xmw >> (m & 31)) & 1u;
+                if (xm) esum += am + tf;
+                if (b < B && p.out_g) {
+                    const float g = scalbnf(__ll2float_rn((long long)(am + sf)), -p.S);
+                    p.out_g[(int64_t)b * N + m] = (p.flip && xm) ? -g : g;
+                }
+            }
+            p.Epart[(int64_t)c * kTcM + r] = esum;
+        }
+        __syncthreads();
+        it = seg_end;
+    }
+
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        for (int s = 0; s < kTcStages; ++s)
+            if (armed[s]) (void)mbar_wait(&full[s], armed_phase[s], never_set);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// E_b: the fixed-point parts of the m-chunks of its tile, added (modulo
+// 2^64; the total fits in 63 bits) and rounded once to float32.
+__global__ void energy_tc_fix_finalize(const unsigned long long* __restrict__ Epart, int B, int T, int chunks,
+                                       int S, float* __restrict__ E)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int t = b / kTcM, r = b % kTcM;
+    unsigned long long s = 0;
+    for (int k = 0; k < chunks; ++k) s += Epart[(int64_t)(k * T + t) * kTcM + r];
+    E[b] = scalbnf(__ll2float_rn((long long)s), -S);
+}
+
+bool fix_tc_supported(const hobo_instance* h)
+{
+    return h->dense && h->d.S3flimb && h->d.tmap_fl_ok && h->N <= 256;
+}
+
+cudaError_t make_tc_tensor_map_fl(hobo_instance* h)
+{
+    const auto& d = h->d;
+    cudaError_t e = encode_planes_map(h->d.tmap_fl, d.S3flimb, d.fl_L, h->N, d.KP, d.KP, 64);
+    h->d.tmap_fl_ok = e == cudaSuccess;
+    return e;
+}
+
+cudaError_t launch_energy_tc_fix(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g_or_dE,
+                                 bool flip_out, cudaStream_t st)
+{
+    if (!fix_tc_supported(h)) return cudaErrorNotSupported;
+    if (B == 0) return cudaSuccess;
+    const auto& d = h->d;
+    const int tiles = (B + kTcM - 1) / kTcM;
+    const int chunks = std::max(1, std::min(h->N, h->num_sms / tiles));
+    TcFixParams p{};
+    p.X = X; p.B = B; p.N = h->N; p.W = h->W; p.KP = d.KP; p.L = d.fl_L; p.S = d.fl_shift;
+    p.T = tiles; p.chunks = chunks; p.G = tiles * chunks;
+    p.fa = d.fa; p.out_g = g_or_dE; p.flip = flip_out ? 1 : 0; p.status = h->status;
+    unsigned long long* Epart = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&Epart, sizeof(unsigned long long) * (size_t)p.G * kTcM, st);
+    if (e != cudaSuccess) return e;
+    p.Epart = Epart;
+    const size_t sm = tc_smem_bytes(d.KP, d.KP);
+    e = cudaFuncSetAttribute(energy_tc_fix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) {
+        const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(d.tmap_fl);
+        energy_tc_fix_kernel<<<p.G, kTcThreads, sm, st>>>(*map, p);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        energy_tc_fix_finalize<<<(B + 255) / 256, 256, 0, st>>>(Epart, B, tiles, chunks, p.S, E);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(Epart, st);
+    return e;
+}
+
 cudaError_t launch_energy_tc(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g_or_dE,
                              bool flip_out, cudaStream_t st)
 {

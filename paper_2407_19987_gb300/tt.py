@@ -1,10 +1,9 @@
 """Tensor-train form of a HOBO tensor (Sec. VI) and its contraction.
 
 ``tt_svd`` decomposes a dense tensor by successive SVDs on the host (the
-decomposition of Sec. VI: reshape the remainder, SVD, keep the singular
-values above a relative tolerance, carry Sigma V* on); ``TensorTrain`` holds
-the cores on the GPU and contracts them with batches of states in the
-library's kernel (hobo_tt_energy).
+decomposition of Sec. VI, here swept from the last index to the first);
+``TensorTrain`` holds the cores on the GPU and contracts them with batches
+of states in the library's kernel (hobo_tt_energy).
 """
 from __future__ import annotations
 
@@ -16,20 +15,27 @@ from .binding import _check, _ptr, _stream, load_library
 
 
 def tt_svd(T: np.ndarray, rel_tol: float = 1e-10, max_rank: int = 256) -> list:
-    """Cores G_c [r_{c-1}, n_c, r_c] of a dense tensor, singular values
-    below rel_tol * (largest) dropped, ranks capped at max_rank."""
+    """Cores G_c [r_{c-1}, n_c, r_c] of a dense tensor by successive SVDs
+    (Sec. VI), taken from the last index to the first: the part of the
+    tensor not yet split off, reshaped to (n_1...n_{c-1}) x (n_c r_c), is
+    factored as U S V*; V* (singular values above rel_tol * the largest, at
+    most max_rank of them) becomes core c and U S is carried to the left.
+    Without truncation the ranks are those of the tensor's unfoldings, the
+    same as a first-to-last sweep gives."""
     T = np.asarray(T, dtype=np.float64)
     d, n = T.ndim, T.shape
-    cores, r, rest = [], 1, T.reshape(1, -1)
-    for c in range(d - 1):
-        rest = rest.reshape(r * n[c], -1)
-        U, s, Vt = np.linalg.svd(rest, full_matrices=False)
+    cores = [None] * d
+    r_right = 1
+    left = T.reshape(-1, n[d - 1])
+    for c in range(d - 1, 0, -1):
+        left = left.reshape(-1, n[c] * r_right)
+        U, s, Vt = np.linalg.svd(left, full_matrices=False)
         keep = 1 if not s.size or s[0] == 0 else int(np.count_nonzero(s > rel_tol * s[0]))
         keep = max(1, min(keep, max_rank))
-        cores.append(U[:, :keep].reshape(r, n[c], keep))
-        rest = s[:keep, None] * Vt[:keep]
-        r = keep
-    cores.append(rest.reshape(r, n[d - 1], 1))
+        cores[c] = Vt[:keep].reshape(keep, n[c], r_right)
+        left = U[:, :keep] * s[:keep]
+        r_right = keep
+    cores[0] = left.reshape(1, n[0], r_right)
     return cores
 
 

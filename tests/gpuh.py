@@ -34,16 +34,31 @@ def abs_instance(inst):
     return W.Instance(inst.N, inst.order, inst.idx, np.abs(inst.coef), inst.offset, inst.integer)
 
 
-# Values whose cancellation condition number scale/|ref| exceeds 64 are held
-# to the absolute bound 1e-5 * scale / 64 (about 2.6 float32 ulps of the sum
-# of magnitudes): no float32 summation of float32 terms can promise a
-# relative error on a result that cancels more deeply than that.
-COND_MAX = 64.0
+# The float bar: err = |got - ref| / max(|ref|, A / COND_MAX) <= 1e-5, with
+# A the sum of |coefficient| over the terms active in that quantity (the
+# floor 2^-10 A of the scope's reading of the relative-error bar).  The
+# exact fixed-point paths (term list, tensor-core limb planes) round each
+# result once, so they meet it with a wide margin.  The kernels that
+# accumulate bf16-split products in float32 (the order-4 tensor-core path,
+# the float32-accumulating order-3 path kept for comparison) carry float32
+# summation error relative to A: they are held to the floor A / 64 (1e-5 of
+# it is 2.6 float32 ulps of A), COND_MAX_F32ACC.
+COND_MAX = 1024.0
+COND_MAX_F32ACC = 64.0
 
 
-def rel_err(got: np.ndarray, ref: np.ndarray, scale: np.ndarray) -> np.ndarray:
-    """|got - ref| / max(|ref|, scale / COND_MAX), scale = sum of
+def rel_err(got: np.ndarray, ref: np.ndarray, scale: np.ndarray, cond_max: float = COND_MAX) -> np.ndarray:
+    """|got - ref| / max(|ref|, scale / cond_max), scale = sum of
     |coefficient| over the terms active in that quantity."""
-    den = np.maximum(np.abs(ref), scale / COND_MAX)
+    den = np.maximum(np.abs(ref), scale / cond_max)
     den = np.where(den == 0, 1.0, den)
     return np.abs(got - ref) / den
+
+
+def fix_shift(abs_sum: float) -> int:
+    """The library's fixed-point scale S: the sum of all |coefficients|
+    times 2^S stays below 2^62."""
+    import math
+    if abs_sum <= 0:
+        return 0
+    return 62 - math.frexp(abs_sum)[1]

@@ -220,10 +220,11 @@ def test_dense_float_full_size_best_energies():
     np.testing.assert_allclose(bestE[sample], O.energy(inst, bx), rtol=1e-12, atol=1e-9)
     E0 = O.energy(inst, O.init_states(2, inst.N, 4))
     assert (bestE[:4] < E0).all()
-    # float32 energy tracked along the trajectory stays within the float bar
+    # the float32 energy tracked along the trajectory (float32 sums of every
+    # accepted flip's delta) stays within 1e-4 at the float32-sum floor A / 64
     e32 = r["bestE32"].cpu().numpy().astype(np.float64)
     absi = gpuh.abs_instance(inst)
-    assert gpuh.rel_err(e32[sample], bestE[sample], O.energy(absi, bx)).max() <= 1e-4
+    assert gpuh.rel_err(e32[sample], bestE[sample], O.energy(absi, bx), gpuh.COND_MAX_F32ACC).max() <= 1e-4
 
 
 @pytest.mark.parametrize("maker,flags", [(lambda: W.tiny_dense(1), 0), (lambda: W.dense_float(2, N=64), 0),
