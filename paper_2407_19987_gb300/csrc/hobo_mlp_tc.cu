@@ -271,14 +271,13 @@ mlp_forward_tc_kernel(const MlpTcParams p)
                 if (threadIdx.x == 128) {
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)buf * bstride;
-                    const uint32_t bk = smem_u32(sB + (size_t)kc * H * 128);
+                    const uint64_t bd = sw128_desc(smem_u32(sB + (size_t)kc * H * 128));
 #pragma unroll
                     for (int pl = 0; pl < 2; ++pl) {
-                        const uint32_t ak = smem_u32(a_hi + pl * 16384);
+                        const uint64_t ad = sw128_desc(smem_u32(a_hi + pl * 16384));
 #pragma unroll
                         for (int ks = 0; ks < kMlpKC / 16; ++ks)
-                            tc_mma(d, sw128_desc(ak + ks * 32), sw128_desc(bk + ks * 32), idesc,
-                                   (kc | pl | ks) != 0 ? 1u : 0u);
+                            tc_mma(d, ad + 2 * ks, bd + 2 * ks, idesc, (kc | pl | ks) != 0 ? 1u : 0u);
                     }
                     tc_commit(&afree[st]);
                     if (kc == nKC - 1) tc_commit(&accfull[buf]);

@@ -186,11 +186,11 @@ energy_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams p)
                                 break;
                             }
                             tc_fence_after();
-                            const uint32_t a0 = smem_u32(sA + kb * 16384);
-                            const uint32_t b0 = smem_u32(sB + cstage * stage_bytes);
+                            const uint64_t ad = sw128_desc(smem_u32(sA + kb * 16384));
+                            const uint64_t bd = sw128_desc(smem_u32(sB + cstage * stage_bytes));
 #pragma unroll
                             for (int k = 0; k < kTcKB / 16; ++k) {
-                                tc_mma(d, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), idesc, accum);
+                                tc_mma(d, ad + 2 * k, bd + 2 * k, idesc, accum);
                                 accum = 1;
                             }
                             tc_commit(&empty[cstage]);
@@ -570,11 +570,11 @@ energy_tc4_kernel(const __grid_constant__ CUtensorMap tmap, const Tc4Params p)
                                 break;
                             }
                             tc_fence_after();
-                            const uint32_t a0 = smem_u32(sA);
-                            const uint32_t b0 = smem_u32(sB + cstage * stage_bytes);
+                            const uint64_t ad = sw128_desc(smem_u32(sA));
+                            const uint64_t bd = sw128_desc(smem_u32(sB + cstage * stage_bytes));
 #pragma unroll
                             for (int k = 0; k < kTcKB / 16; ++k) {
-                                tc_mma(d, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), idesc, accum);
+                                tc_mma(d, ad + 2 * k, bd + 2 * k, idesc, accum);
                                 accum = 1;
                             }
                             tc_commit(&empty[cstage]);
@@ -893,11 +893,11 @@ energy_tc_exact_kernel(const __grid_constant__ CUtensorMap tmap, const TcExactPa
                                 break;
                             }
                             tc_fence_after();
-                            const uint32_t a0 = smem_u32(sA + kb * 16384);
-                            const uint32_t b0 = smem_u32(sB + cstage * stage_bytes);
+                            const uint64_t ad = sw128_desc(smem_u32(sA + kb * 16384));
+                            const uint64_t bd = sw128_desc(smem_u32(sB + cstage * stage_bytes));
 #pragma unroll
                             for (int k = 0; k < kTcKB / 16; ++k) {
-                                tc_mma(d, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), idesc, accum);
+                                tc_mma(d, ad + 2 * k, bd + 2 * k, idesc, accum);
                                 accum = 1;
                             }
                             tc_commit(&empty[cstage]);
@@ -1256,11 +1256,11 @@ energy_tc_fix_kernel(const __grid_constant__ CUtensorMap tmap, const TcFixParams
                             }
                             tc_fence_after();
                             const uint32_t idesc = idesc_bf16(kTcM, 64 * (kb + 1));
-                            const uint32_t a0 = smem_u32(sA + kb * 16384);
-                            const uint32_t b0 = smem_u32(sB + cstage * stage_bytes);
+                            const uint64_t ad = sw128_desc(smem_u32(sA + kb * 16384));
+                            const uint64_t bd = sw128_desc(smem_u32(sB + cstage * stage_bytes));
 #pragma unroll
                             for (int k = 0; k < kTcKB / 16; ++k) {
-                                tc_mma(d, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), idesc, accum);
+                                tc_mma(d, ad + 2 * k, bd + 2 * k, idesc, accum);
                                 accum = 1;
                             }
                             tc_commit(&empty[cstage]);

@@ -55,16 +55,24 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 // Bounded wait: false after limit_ns or once another thread has aborted.
-static __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                       uint64_t limit_ns = kWaitNs)
+// The first try is inline (the common case in a pipeline that keeps up);
+// the polling loop is a call.
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                                  uint64_t limit_ns)
 {
-    if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
         if (global_ns() - t0 > limit_ns) return false;
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t limit_ns = kWaitNs)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    return mbar_wait_slow(bar, parity, abort_flag, limit_ns);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
@@ -118,7 +126,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
-// 8-row core groups 1024 bytes apart (SBO), descriptor version 1.
+// 8-row core groups 1024 bytes apart (SBO), descriptor version 1.  The
+// start address sits in the low 14 bits in 16-byte units, so the
+// descriptor of an operand 32 bytes further along K (the next K = 16 step
+// inside a 128-byte swizzle atom) is this one plus 2.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 {
     uint64_t d = 0;
