@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--case-offset", type=int, default=0, help="first sweep of the schedule in the sweep case")
     ap.add_argument("--clocks-csv", default=None, help="also write the raw clock samples of the timed region here")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-workload measurement")
+    ap.add_argument("--learned-train", type=int, default=64, help="training instances of the proposal network")
+    ap.add_argument("--learning-curve", action="store_true",
+                    help="only the proposal network's learning curve (16..1024 training instances), one JSON line each")
     return ap.parse_args()
 
 
@@ -364,9 +367,10 @@ def run_ours(a):
         line["contraction"] = measure_dense_contraction(h, inst, B)
     if rank == 0 and not a.no_extras:
         line["time_to_target"] = measure_time_to_target_dense(h, B)
-        line["extras"] = {"uneven_batch": measure_uneven_batch(),
+        line["extras"] = {"tiny_time_to_target": measure_time_to_target_tiny(),
+                          "uneven_batch": measure_uneven_batch(),
                           "int_encoded": measure_int_encoded(),
-                          "learned_proposal": measure_learned(),
+                          "learned_proposal": measure_learned(a.learned_train),
                           "tensor_train": measure_tt(),
                           "order4_contraction": measure_tc4()}
     if rank == 0 and not a.no_cpu_baseline:
@@ -421,15 +425,87 @@ def measure_uneven_batch(plain_sample: int = 8):
     p_rate = sub_flips / (p_ms_sub / 1000.0)
     shape = bt.launch_shape(0)
     acc = int(bt.anneal(seeds[:len(bt.B)], betas, mode=H.HOBO_BATCH_GRAPH, want_accepts=True)["accepts"].sum().item())
-    return {"workload": "uneven_batch: 512 order-3 instances, N~U[16,192], 5% density, N(0,1), "
-                        "B=1024 each, 500 sweeps, T 5->0.02",
-            "attempted_flips": flips, "accepted_flips": acc,
-            "graph_ms": g_ms, "graph_flips_per_s": flips / (g_ms / 1000.0),
-            "per_instance_tuned_ms": t_ms, "per_instance_tuned_flips_per_s": flips / (t_ms / 1000.0),
-            "per_instance_plain_flips_per_s": p_rate,
-            "per_instance_plain_sample": f"first {plain_sample} instances ({sub_flips} flips, {p_ms_sub:.1f} ms)",
-            "speedup_graph_vs_plain": (flips / (g_ms / 1000.0)) / p_rate,
-            "autotuned_shape": {"warps_per_cta": shape[0], "ctas": shape[1]}}
+    out = {"workload": "uneven_batch: 512 order-3 instances, N~U[16,192], 5% density, N(0,1), "
+                       "B=1024 each, 500 sweeps, T 5->0.02",
+           "attempted_flips": flips, "accepted_flips": acc,
+           "graph_ms": g_ms, "graph_flips_per_s": flips / (g_ms / 1000.0),
+           "per_instance_tuned_ms": t_ms, "per_instance_tuned_flips_per_s": flips / (t_ms / 1000.0),
+           "per_instance_plain_flips_per_s": p_rate,
+           "per_instance_plain_sample": f"first {plain_sample} instances ({sub_flips} flips, {p_ms_sub:.1f} ms)",
+           "speedup_graph_vs_plain": (flips / (g_ms / 1000.0)) / p_rate,
+           "autotuned_shape": {"warps_per_cta": shape[0], "ctas": shape[1]}}
+
+    # time to solution over the whole batch: per-instance targets = lowest
+    # energy of 64 runs x 20000 sweeps of that instance (one graph launch)
+    long = H.Batch(hs, [64] * len(hs))
+    r, long_ms = _timed_ms(lambda: long.anneal(seeds, W.geometric_betas(T0, T1, 20000), mode=H.HOBO_BATCH_GRAPH))
+    targets = np.array([float(long.rows(r["bestE"], t).min().item()) for t in range(len(hs))])
+    long.close()
+
+    def rung(bt_, Sx, mode, n):
+        rr, ms = _timed_ms(lambda: bt_.anneal(seeds[:n], W.geometric_betas(T0, T1, Sx), mode=mode))
+        p = np.array([float((bt_.rows(rr["bestE"], t).cpu().numpy() <= targets[t]).mean()) for t in range(n)])
+        return p, ms
+
+    ladder = (5, 10, 20, 50, 100, 200, 500, 1000)
+    # size the schedule buffers for the longest rung first (no graph rebuild
+    # inside a timed call)
+    bt.anneal(seeds, W.geometric_betas(T0, T1, ladder[-1]), mode=H.HOBO_BATCH_GRAPH)
+    torch.cuda.synchronize()
+    rungs = []
+    for Sx in ladder:
+        pk, ms = rung(bt, Sx, H.HOBO_BATCH_GRAPH, len(hs))
+        runs = runs_for_all_99(pk)
+        rungs.append({"sweeps": Sx, "graph_ms": ms, "instances_reached": int((pk > 0).sum()),
+                      "min_p_success": float(pk.min()), "mean_p_success": float(pk.mean()),
+                      "runs_for_all_99": runs, "tts99_ms": None if runs is None else ms / B * runs})
+    ok = [x for x in rungs if x["tts99_ms"] is not None]
+    best = min(ok, key=lambda x: x["tts99_ms"]) if ok else None
+    plain = None
+    if best is not None:
+        # the plain per-instance form at the same length on the sample, its
+        # time scaled to the batch by attempted flips; its decisions equal
+        # the batch kernel's, so the sample's success rates must match
+        pk_s, ms_s = rung(sub, best["sweeps"], H.HOBO_BATCH_PER_INSTANCE_PLAIN, plain_sample)
+        pk_g, _ = rung(bt, best["sweeps"], H.HOBO_BATCH_GRAPH, len(hs))
+        ms_plain = ms_s * flips / sub_flips
+        plain = {"sweeps": best["sweeps"], "ms_scaled_to_batch": ms_plain,
+                 "same_p_as_graph_on_sample": bool(np.array_equal(pk_s, pk_g[:plain_sample])),
+                 "tts99_ms": ms_plain / B * best["runs_for_all_99"]}
+    out["time_to_target"] = {"targets_from": "per instance, best of 64 runs x 20000 sweeps", "targets_ms": long_ms,
+                             "tts_definition": "runs r such that every instance reaches its target with "
+                                               "probability >= 0.99 (prod_k 1 - (1 - p_k)^r), "
+                                               "TTS99 = graph time / B * r",
+                             "rungs": rungs, "best": best, "per_instance_plain": plain,
+                             "speedup_tts99_graph_vs_plain": (plain["tts99_ms"] / best["tts99_ms"]) if plain else None}
+    sub.close()
+    bt.close()
+    return out
+
+
+def runs_for_all_99(p):
+    """Smallest (real) number of independent runs r with
+    prod_k (1 - (1 - p_k)^r) >= 0.99, i.e. every instance k reaches its
+    target with 99% confidence; None if some p_k = 0."""
+    p = np.asarray(p, dtype=np.float64)
+    if p.size == 0 or (p <= 0).any():
+        return None
+
+    def ok(r):
+        return float(np.sum(np.log1p(-np.power(1.0 - p, r)))) >= np.log(0.99) if (p < 1).any() else True
+
+    if ok(1.0):
+        return 1.0
+    lo, hi = 1.0, 2.0
+    while not ok(hi):
+        lo, hi = hi, hi * 2.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if ok(mid):
+            hi = mid
+        else:
+            lo = mid
+    return hi
 
 
 SWEEP_SOURCES = ("paper_2407_19987_gb300/csrc/sweep_impl.cuh", "paper_2407_19987_gb300/csrc/sweep_dense.cu",
@@ -538,29 +614,66 @@ def _timed_ms(fn):
     return out, e0.elapsed_time(e1)
 
 
-LADDER = (5, 10, 15, 20, 25, 35, 50, 70, 100, 140, 200, 280, 400, 560, 800, 1120, 1600, 2240, 3200)
+LADDER = (5, 10, 20, 50, 100, 200, 500, 1000, 2000)
 
 
-def _ladder(run, target, ladder=LADDER):
-    """Schedules of growing length; the first whole anneal (time of the
-    call: initial states, contraction, sweeps, float64 re-score) whose best
-    state reaches the target."""
-    missed = 0.0
+def runs_for_99(p: float):
+    """Independent runs needed for a 99% chance that at least one succeeds,
+    when one succeeds with probability p: ln(0.01) / ln(1 - p), at least 1
+    (None when p = 0)."""
+    import math
+    if p <= 0.0:
+        return None
+    if p >= 0.99:
+        return 1.0
+    return math.log(0.01) / math.log1p(-p)
+
+
+def tts_ladder(run, target, B: int, ladder=LADDER):
+    """Time to solution.  Each rung S is a fresh anneal of B independent
+    states over an S-sweep schedule; p(S) is the share of states whose best
+    energy reaches the target, t(S) the CUDA-event time of the whole call
+    (initial states, contraction, sweeps, float64 re-score).  The time a run
+    costs on this GPU is t(S) / B, and a run succeeds with probability p(S),
+    so TTS99(S) = t(S) / B * ln(0.01) / ln(1 - p(S)) is the time to reach the
+    target with 99% confidence.  The optimum over S is the figure of merit:
+    it trades a run's length against its chance of success, so it is not
+    decided by the first rung."""
+    rungs = []
     for S in ladder:
         E, ms = run(S)
-        if float(E.min()) <= target:
-            return {"sweeps": S, "ms": ms, "ms_including_misses": missed + ms, "best": float(E.min())}
-        missed += ms
-    return {"sweeps": None, "ms": None, "ms_including_misses": missed, "best": float(E.min())}
+        p = float(np.mean(E <= target))
+        r99 = runs_for_99(p)
+        rungs.append({"sweeps": S, "ms": ms, "p_success": p,
+                      "tts99_ms": None if r99 is None else ms / B * r99, "best": float(E.min())})
+    ok = [r for r in rungs if r["tts99_ms"] is not None]
+    best = min(ok, key=lambda r: r["tts99_ms"]) if ok else None
+    return {"rungs": rungs, "best": best}
+
+
+def _plain_at(best, run_plain, B: int):
+    """The plain FP32 form at the tuned form's optimal schedule length: its
+    trajectories are the tuned form's (same decisions), so its success rate
+    is measured and must equal the tuned one's; its TTS99 uses its own time."""
+    if best is None:
+        return None
+    E, ms, p = run_plain(best["sweeps"])
+    r99 = runs_for_99(p)
+    return {"sweeps": best["sweeps"], "ms": ms, "p_success": p, "same_p_as_tuned": p == best["p_success"],
+            "tts99_ms": None if r99 is None else ms / B * r99}
+
+
+def _speedup(plain, best):
+    if plain is None or best is None or plain["tts99_ms"] is None:
+        return None
+    return plain["tts99_ms"] / best["tts99_ms"]
 
 
 def measure_time_to_target_dense(h, B: int):
-    """Time to target on the dense N=256 workload: target = lowest energy of
-    64 long runs (20000 sweeps, T 10 -> 0.01) of the annealer; then schedules
-    of growing length on B states, tuned sweep vs the plain FP32 sweep (one
-    thread per state, fields in global memory).  The two sweeps make the same
-    decisions, so the plain form is timed at the length where the tuned one
-    first reaches the target (and its best energy is checked equal)."""
+    """Time to solution on the dense N=256 workload: target = lowest energy
+    of 64 long runs (20000 sweeps, T 10 -> 0.01) of the annealer; tuned sweep
+    vs the plain FP32 sweep (one thread per state, fields in global
+    memory)."""
     import paper_2407_19987_gb300 as H
     T0, T1, _, _ = W.SCHEDULES["dense_float"]
     r, long_ms = _timed_ms(lambda: h.anneal(77, 64, W.geometric_betas(T0, T1, 20000)))
@@ -570,16 +683,49 @@ def measure_time_to_target_dense(h, B: int):
         rr, ms = _timed_ms(lambda: h.anneal(5, B, W.geometric_betas(T0, T1, S), mode=mode))
         return rr["bestE"].cpu().numpy(), ms
 
-    tuned = _ladder(run, target)
-    plain = None
-    if tuned["sweeps"] is not None:
-        E, ms = run(tuned["sweeps"], H.HOBO_ANNEAL_PLAIN)
-        plain = {"sweeps": tuned["sweeps"], "ms": ms, "best": float(E.min()),
-                 "same_best_as_tuned": float(E.min()) == tuned["best"]}
-    return {"workload": f"dense_float N=256, B={B}, geometric T {T0}->{T1}, schedule lengths {LADDER[0]}..{LADDER[-1]}",
+    def run_plain(S):
+        E, ms = run(S, H.HOBO_ANNEAL_PLAIN)
+        return E, ms, float(np.mean(E <= target))
+
+    tuned = tts_ladder(run, target, B)
+    plain = _plain_at(tuned["best"], run_plain, B)
+    return {"workload": f"dense_float N=256, B={B} runs per call, geometric T {T0}->{T1}, "
+                        f"schedule lengths {list(LADDER)}",
             "target": target, "target_from": "best of 64 runs x 20000 sweeps", "target_ms": long_ms,
-            "tuned": tuned, "plain_fp32": plain,
-            "speedup_tuned_vs_plain": (plain["ms"] / tuned["ms"]) if plain else None}
+            "tuned": tuned, "plain_fp32": plain, "speedup_tts99_tuned_vs_plain": _speedup(plain, tuned["best"])}
+
+
+def measure_time_to_target_tiny():
+    """Time to solution on the tiny workload (order 3, N=12, integer
+    coefficients, B=256 runs per call, T 5 -> 0.05): the target is the
+    ground energy, found by evaluating all 4096 states with the library's
+    float64 re-score; tuned vs plain FP32."""
+    import torch
+
+    import paper_2407_19987_gb300 as H
+    inst = W.tiny_dense(1)
+    T0, T1, _, B = W.SCHEDULES["tiny_dense"]
+    h = H.Instance.from_terms(inst.idx, inst.coef, inst.N, H.HOBO_INTEGER)
+    allX = np.array([[(s >> i) & 1 for i in range(inst.N)] for s in range(1 << inst.N)], np.uint8)
+    Xd = torch.from_numpy(W.pack_bits(allX).view(np.int32)).cuda()
+    target = float(h.energy_fp64(Xd).min().item())
+
+    def run(S, mode=H.HOBO_ANNEAL_TUNED):
+        rr, ms = _timed_ms(lambda: h.anneal(1, B, W.geometric_betas(T0, T1, S), mode=mode))
+        return rr["bestE"].cpu().numpy(), ms
+
+    def run_plain(S):
+        E, ms = run(S, H.HOBO_ANNEAL_PLAIN)
+        return E, ms, float(np.mean(E <= target))
+
+    ladder = (1, 2, 5, 10, 20, 50, 100)
+    tuned = tts_ladder(run, target, B, ladder)
+    plain = _plain_at(tuned["best"], run_plain, B)
+    h.close()
+    return {"workload": f"tiny_dense: order 3, N=12, integer coefficients, B={B} runs per call, T {T0}->{T1}, "
+                        f"schedule lengths {list(ladder)}",
+            "target": target, "target_from": "ground energy over all 4096 states (library float64 re-score)",
+            "tuned": tuned, "plain_fp32": plain, "speedup_tts99_tuned_vs_plain": _speedup(plain, tuned["best"])}
 
 
 def measure_int_encoded():
@@ -602,40 +748,68 @@ def measure_int_encoded():
                        f"{S} sweeps, T {T0}->{T1}",
            "ms": m, "flips_per_s": B * inst.N * S / (m / 1000.0), "accepted_per_step": acc,
            "best_objective": best}
+    # time to solution: target = lowest energy of 64 runs x 20000 sweeps
+    r, long_ms = _timed_ms(lambda: h.anneal(77, 64, W.geometric_betas(T0, T1, 20000)))
+    target = float(r["bestE"].min().item())
+
+    def run(Sx, mode=H.HOBO_ANNEAL_TUNED):
+        rr, t = _timed_ms(lambda: h.anneal(5, B, W.geometric_betas(T0, T1, Sx), mode=mode))
+        return rr["bestE"].cpu().numpy(), t
+
+    def run_plain(Sx):
+        E, t = run(Sx, H.HOBO_ANNEAL_PLAIN)
+        return E, t, float(np.mean(E <= target))
+
+    tuned = tts_ladder(run, target, B)
+    plain = _plain_at(tuned["best"], run_plain, B)
+    out["time_to_target"] = {"target": target, "target_objective": target + inst.offset,
+                             "target_from": "best of 64 runs x 20000 sweeps", "target_ms": long_ms,
+                             "schedule_lengths": list(LADDER), "tuned": tuned, "plain_fp32": plain,
+                             "speedup_tts99_tuned_vs_plain": _speedup(plain, tuned["best"])}
     h.close()
     return out
 
 
-def measure_learned(n_train: int = 64, test_seeds=(5000, 5001, 5002, 5003)):
-    """The learned proposal on the sparse order-4 workload (N=96, 2%
-    density, integer coefficients): train the network (H=256) on recorded
-    plain-annealer trajectories of n_train seeded instances, then on each
-    test instance compare, at B=4096, time to target (lowest energy of 64
-    runs x 20000 sweeps + 0.5%) for the tuned sweep, the learned sweep and
-    the plain FP32 sweep, and the share of states reaching the target at
-    100 and 500 sweeps."""
+LEARNED_FORMS = (("learned_order", dict(plain_every=4, select=0, top_frac=1.0)),
+                 ("learned_threshold_m1", dict(plain_every=4, select=1, threshold=-1.0)),
+                 ("learned_threshold_m3", dict(plain_every=4, select=1, threshold=-3.0)))
+
+
+def train_proposal(n_train: int, seed0: int = 10 ** 6, steps: int = 3000, batch: int = 8192):
+    """Record plain-annealer trajectories of n_train seeded instances of the
+    sparse order-4 workload (256 states each, 500 sweeps, every 5th sweep,
+    16 states recorded) and train the H=256 network on them."""
     import torch
 
     import paper_2407_19987_gb300 as H
     from paper_2407_19987_gb300 import learned as LP
-    T0, T1, S, B = W.SCHEDULES["sparse_order4"]
+    T0, T1, _, _ = W.SCHEDULES["sparse_order4"]
     t = time.perf_counter()
-    train = [W.sparse_order4(10 ** 6 + k) for k in range(n_train)]
+    train = [W.sparse_order4(seed0 + k) for k in range(n_train)]
     hs = [H.Instance.from_terms(i.idx, i.coef, i.N) for i in train]
     gen_s = time.perf_counter() - t
-    (F, y), rec_ms = _timed_ms(lambda: LP.record(hs, seed=10 ** 6, B=256, betas=W.geometric_betas(T0, T1, 500),
+    (F, y), rec_ms = _timed_ms(lambda: LP.record(hs, seed=seed0, B=256, betas=W.geometric_betas(T0, T1, 500),
                                                   rec_every=5, rec_states=16))
     for hh in hs:
         hh.close()
     net = H.MLP(256, seed=1)
     loss0 = LP.full_loss(net, F, y)
-    steps, batch = 3000, 8192
     _, train_ms = _timed_ms(lambda: LP.train(net, F, y, steps=steps, batch=batch, lr=1e-3, seed=1))
     loss1 = LP.full_loss(net, F, y)
     rows = int(F.shape[0])
     del F, y
     torch.cuda.empty_cache()
-    learned_kw = dict(plain_every=4, select=H.SELECT_ORDER, top_frac=1.0)
+    return net, {"instances": n_train, "rows": rows, "record_ms": rec_ms, "gen_s": gen_s, "steps": steps,
+                 "batch": batch, "train_ms": train_ms, "loss_before": loss0, "loss_after": loss1}
+
+
+def learned_tts(net, test_seeds, forms=LEARNED_FORMS, with_plain: bool = True):
+    """Per test instance of the sparse order-4 workload: target = lowest
+    energy of 64 runs x 20000 sweeps + 0.5%; TTS99 ladders (B=4096 runs per
+    call) of the tuned sweep and of the learned sweep in each form; the
+    plain FP32 form at the tuned optimum."""
+    import paper_2407_19987_gb300 as H
+    T0, T1, _, B = W.SCHEDULES["sparse_order4"]
     per = []
     for seed in test_seeds:
         inst = W.sparse_order4(seed)
@@ -648,36 +822,63 @@ def measure_learned(n_train: int = 64, test_seeds=(5000, 5001, 5002, 5003)):
             rr, ms = _timed_ms(lambda: h.anneal(11, B, W.geometric_betas(T0, T1, Sx), mode=mode))
             return rr["bestE"].cpu().numpy(), ms
 
-        def learned(Sx):
-            rr, ms = _timed_ms(lambda: H.anneal_learned(h, net, 11, B, W.geometric_betas(T0, T1, Sx), **learned_kw))
-            return rr["bestE"].cpu().numpy(), ms
+        def run_plain(Sx):
+            E, ms = tuned(Sx, H.HOBO_ANNEAL_PLAIN)
+            return E, ms, float(np.mean(E <= target))
 
-        res = {"seed": seed, "target": target, "tuned": _ladder(tuned, target), "learned": _ladder(learned, target)}
-        if res["tuned"]["sweeps"] is not None:
-            E, ms = tuned(res["tuned"]["sweeps"], H.HOBO_ANNEAL_PLAIN)
-            res["plain_fp32"] = {"sweeps": res["tuned"]["sweeps"], "ms": ms, "best": float(E.min())}
-        for Sx in (100, 500):
-            for name, fn in (("tuned", tuned), ("learned", learned)):
-                E, ms = fn(Sx)
-                res[f"{name}_S{Sx}"] = {"ms": ms, "mean_best": float(E.mean()), "hit_frac": float((E <= target).mean())}
+        res = {"seed": seed, "target": target, "tuned": tts_ladder(tuned, target, B)}
+        for name, kw in forms:
+            def learned(Sx, kw=kw):
+                rr, ms = _timed_ms(lambda: H.anneal_learned(h, net, 11, B, W.geometric_betas(T0, T1, Sx), **kw))
+                return rr["bestE"].cpu().numpy(), ms
+            res[name] = tts_ladder(learned, target, B)
+        if with_plain:
+            res["plain_fp32"] = _plain_at(res["tuned"]["best"], run_plain, B)
         per.append(res)
         h.close()
-    network = measure_network_pass(net)
-    net.close()
+    keys = ["tuned"] + [n for n, _ in forms] + (["plain_fp32"] if with_plain else [])
 
     def gm(key):
-        v = [p[key]["ms"] for p in per if p.get(key) and p[key].get("ms")]
-        return float(np.exp(np.mean(np.log(v)))) if len(v) == len(per) else None
+        v = []
+        for p in per:
+            x = p.get(key)
+            x = x.get("best", x) if isinstance(x, dict) and "rungs" in x else x
+            if not x or x.get("tts99_ms") is None:
+                return None
+            v.append(x["tts99_ms"])
+        return float(np.exp(np.mean(np.log(v))))
 
-    return {"workload": f"sparse_order4: order 4, N=96, 2% density, integers in [-8,8], B={B}, "
+    return per, {k: gm(k) for k in keys}
+
+
+def measure_learned(n_train: int = 64, test_seeds=(5000, 5001, 5002, 5003)):
+    """The learned proposal on the sparse order-4 workload (N=96, 2%
+    density, integer coefficients): the network (H=256) trained on recorded
+    plain-annealer trajectories of n_train seeded instances; on each test
+    instance TTS99 of the tuned sweep, of the learned sweep (order and
+    threshold selection) and of the plain FP32 sweep."""
+    net, training = train_proposal(n_train)
+    per, geo = learned_tts(net, test_seeds)
+    network = measure_network_pass(net)
+    net.close()
+    T0, T1, _, B = W.SCHEDULES["sparse_order4"]
+    return {"workload": f"sparse_order4: order 4, N=96, 2% density, integers in [-8,8], B={B} runs per call, "
                         f"geometric T {T0}->{T1}; test seeds {list(test_seeds)}",
-            "training": {"instances": n_train, "rows": rows, "record_ms": rec_ms, "gen_s": gen_s,
-                         "steps": steps, "batch": batch, "train_ms": train_ms, "loss_before": loss0,
-                         "loss_after": loss1},
-            "learned_opts": {k: v for k, v in learned_kw.items()},
-            "per_instance": per,
-            "geomean_ttt_ms": {"tuned": gm("tuned"), "learned": gm("learned"), "plain_fp32": gm("plain_fp32")},
-            "network_pass": network}
+            "training": training, "forms": {k: v for k, v in LEARNED_FORMS},
+            "per_instance": per, "geomean_tts99_ms": geo, "network_pass": network}
+
+
+def learning_curve(sizes=(16, 64, 256, 1024), test_seeds=(5000, 5001, 5002, 5003)):
+    """Training loss and TTS99 of the learned forms against the number of
+    training instances (same test instances and ladders as the bench)."""
+    out = []
+    for n in sizes:
+        net, training = train_proposal(n)
+        _, geo = learned_tts(net, test_seeds, with_plain=False)
+        net.close()
+        out.append({"train_instances": n, "training": training, "geomean_tts99_ms": geo})
+        print(json.dumps(out[-1]), flush=True)
+    return out
 
 
 def measure_network_pass(net, S: int = 500, G: int = 256, n_rows: int = 1 << 20, reps: int = 5):
@@ -894,6 +1095,9 @@ def main():
     a = parse()
     if a.kernel_case:
         return run_kernel_case(a)
+    if a.learning_curve:
+        learning_curve()
+        return 0
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)
