@@ -488,10 +488,33 @@ SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
     return p;
 }
 
+// Dense instances run the schedule in two launches: the first tenth of the
+// sweeps (at least kSplitMin, the high-temperature descent where nearly
+// every state flips often and the slab reads are L2-bandwidth bound) with
+// the plain update, the rest (few flips, often the same bit back and forth)
+// with reuse of the last update vector.  The second launch resumes from the
+// first one's states, fields and energies in global memory, so the result
+// is that of one launch bit for bit.
+constexpr int kSplitMin = 16;
+
 cudaError_t launch_sweep_tuned(const hobo_instance* h, const SweepArgs& a, cudaStream_t st)
 {
     if (a.B == 0 || a.sweeps == 0) return cudaSuccess;
     const SweepDev p = make_dev(h, a);
+    if (h->dense && a.g && a.sweeps > 2 * kSplitMin) {
+        const int s1 = std::max(kSplitMin, a.sweeps / 10);
+        SweepArgs a1 = a;
+        a1.sweeps = s1;
+        a1.write_g = true;
+        cudaError_t e = dispatch_tuned<true, 1>(make_dev(h, a1), st);
+        if (e != cudaSuccess) return e;
+        SweepArgs a2 = a;
+        a2.beta = a.beta + s1;
+        a2.sweeps = a.sweeps - s1;
+        a2.sweep0 = a.sweep0 + s1;
+        a2.resume = 1;
+        return dispatch_tuned_dense_reuse(make_dev(h, a2), st);
+    }
     if (h->dense) return dispatch_tuned<true, 1>(p, st);
     if (h->KU <= 1) return dispatch_tuned<false, 1>(p, st);
     if (h->KU <= 2) return dispatch_tuned<false, 2>(p, st);

@@ -83,10 +83,10 @@ constexpr int kTunedMinBlocks = 27;
 // at most N/2 rows are read.  Lanes own 4 consecutive targets in each
 // 128-wide chunk (NC chunks); rows are visited in ascending order, 8 at a
 // time with their loads in flight together.
-template <int WMAX, int NC>
+template <int WMAX, int NC, bool CACHE = false>
 __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __restrict__ g,
                                                 const uint32_t (&x)[WMAX], int i, float delta, int lane,
-                                                uint32_t* __restrict__ rows)
+                                                uint32_t* __restrict__ rows, float* __restrict__ cache = nullptr)
 {
     const int N = p.N, P = p.P, W = p.W;
     const float* __restrict__ slab = p.S3 + (int64_t)i * N * P;
@@ -168,10 +168,31 @@ __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __rest
         const float a4[4] = {d.x, d.y, d.z, d.w};
         const float s4[4] = {s2.x, s2.y, s2.z, s2.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (j + q < N) g[j + q] = __fadd_rn(g[j + q], __fmul_rn(delta, __fadd_rn(s4[q], a4[q])));
+        for (int q = 0; q < 4; ++q) {
+            const float u = __fadd_rn(s4[q], a4[q]);
+            if (j + q < N) g[j + q] = __fadd_rn(g[j + q], __fmul_rn(delta, u));
+            if (CACHE && j + q < N) cache[j + q] = u;
+        }
     }
     return bytes;
+}
+
+// Late-phase reuse of the update vector.  The vector of a flip of bit i,
+// u_j = S2[i][j] + (sum over the row list of S3[i][l][j]), does not depend
+// on x_i: slab i's row i is zero, so when the next accepted flip of a state
+// is bit i again (no other bit changed in between) and the choice between
+// set rows and clear rows is the same, its row list differs only by that
+// zero row, and adding +0 to a sum that is never -0 changes nothing.  The
+// same float vector then comes out, and the state's last vector, kept in
+// shared memory, is applied instead of reading the rows again.  With x
+// already flipped:
+template <int WMAX>
+__device__ __forceinline__ bool dense_comp(const uint32_t (&x)[WMAX], int N)
+{
+    int pop = 0;
+#pragma unroll
+    for (int k = 0; k < WMAX; ++k) pop += __popc(x[k]);
+    return 2 * pop > N;
 }
 
 // Sparse update for a flip of bit i: lanes take the target records of a
@@ -279,15 +300,24 @@ __host__ __device__ constexpr int warp_region_floats(int N, int WMAX)
     return 2 * ((N + 3) & ~3) + 4 * (WMAX + 1) + 8;
 }
 
+// The same plus the last update vector (late-phase dense sweep).
+__host__ __device__ constexpr int warp_region_floats_reuse(int N, int WMAX)
+{
+    return warp_region_floats(N, WMAX) + ((N + 3) & ~3);
+}
+
 // The whole anneal of state b of the instance described by p, run by one
 // warp whose shared-memory region starts at g.
-template <int WMAX, bool DENSE, int KU, bool PAIRED = false>
+template <int WMAX, bool DENSE, int KU, bool PAIRED = false, bool REUSE = false>
 __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g, int lane)
 {
     const int N = p.N, W = p.W;
     const int NPAD = (N + 3) & ~3;
     uint32_t* bs = reinterpret_cast<uint32_t*>(g + NPAD);   // bits + sentinel (sparse lookups)
     uint32_t* rows = bs + 4 * (WMAX + 1);                   // dense: offsets of the rows to read
+    float* ucache = g + warp_region_floats(N, WMAX);        // REUSE: last update vector
+    int last_bit = -1;                                      // REUSE: its bit (warp-uniform)
+    bool last_comp = false;
 
     for (int j = lane; j < N; j += 32) g[j] = p.g[(int64_t)b * N + j];
     uint32_t x[WMAX];
@@ -360,7 +390,18 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                     for (int k = lane; k < W; k += 32) bxs[k] = sel_word(x, k);
                 }
                 const int fi = 32 * w + f;
-                if (DENSE) {
+                if (DENSE && REUSE) {
+                    const bool comp = dense_comp(x, N);
+                    if (fi == last_bit && comp == last_comp) {
+                        for (int j = lane; j < N; j += 32) g[j] = __fadd_rn(g[j], __fmul_rn(delta, ucache[j]));
+                    } else {
+                        __syncwarp();
+                        nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1), true>(p, g, x, fi, delta, lane,
+                                                                                      rows, ucache);
+                        last_bit = fi;
+                        last_comp = comp;
+                    }
+                } else if (DENSE) {
                     nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1)>(p, g, x, fi, delta, lane, rows);
                 } else {
                     if (lane == 0) bs[w] = cw | (w == wsent ? sent : 0u);
@@ -390,7 +431,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
     }
 }
 
-template <int WMAX, bool DENSE, int KU>
+template <int WMAX, bool DENSE, int KU, bool REUSE = false>
 __global__ void __launch_bounds__(kTunedWarps * 32, kTunedMinBlocks)
 sweep_tuned_kernel(const SweepDev p)
 {
@@ -398,7 +439,8 @@ sweep_tuned_kernel(const SweepDev p)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int b = blockIdx.x * kTunedWarps + warp;       // state of this warp
     if (b >= p.B) return;                                // warp-uniform; no block barriers below
-    anneal_state<WMAX, DENSE, KU>(p, b, sm + (size_t)warp * warp_region_floats(p.N, WMAX), lane);
+    const int rf = REUSE ? warp_region_floats_reuse(p.N, WMAX) : warp_region_floats(p.N, WMAX);
+    anneal_state<WMAX, DENSE, KU, false, REUSE>(p, b, sm + (size_t)warp * rf, lane);
 }
 
 // Batched form: a persistent grid whose warps take (instance, state) work
@@ -705,12 +747,13 @@ template <> cudaError_t dispatch_learned<false, 1>(const SweepDev&, const Learne
 template <> cudaError_t dispatch_learned<false, 2>(const SweepDev&, const LearnedDev&, cudaStream_t);
 template <> cudaError_t dispatch_learned<false, 6>(const SweepDev&, const LearnedDev&, cudaStream_t);
 
-template <int WMAX, bool DENSE, int KU>
+template <int WMAX, bool DENSE, int KU, bool REUSE = false>
 inline cudaError_t run_tuned(const SweepDev& p, cudaStream_t st)
 {
-    const size_t per_warp = sizeof(float) * (size_t)warp_region_floats(p.N, WMAX);
+    const size_t per_warp =
+        sizeof(float) * (size_t)(REUSE ? warp_region_floats_reuse(p.N, WMAX) : warp_region_floats(p.N, WMAX));
     const size_t sm = per_warp * kTunedWarps;
-    auto kern = sweep_tuned_kernel<WMAX, DENSE, KU>;
+    auto kern = sweep_tuned_kernel<WMAX, DENSE, KU, REUSE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
 
@@ -730,6 +773,8 @@ template <> cudaError_t dispatch_batch<false, 6>(const SweepDev*, const int2*, i
 
 template <bool DENSE, int KU>
 cudaError_t dispatch_tuned(const SweepDev& p, cudaStream_t st);
+// dense slabs, late phase: the tuned sweep with reuse of the last update vector
+cudaError_t dispatch_tuned_dense_reuse(const SweepDev& p, cudaStream_t st);
 template <> cudaError_t dispatch_tuned<true, 1>(const SweepDev& p, cudaStream_t st);
 template <> cudaError_t dispatch_tuned<false, 1>(const SweepDev& p, cudaStream_t st);
 template <> cudaError_t dispatch_tuned<false, 2>(const SweepDev& p, cudaStream_t st);
