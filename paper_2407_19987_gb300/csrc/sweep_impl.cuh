@@ -83,10 +83,26 @@ constexpr int kTunedMinBlocks = 27;
 // at most N/2 rows are read.  Lanes own 4 consecutive targets in each
 // 128-wide chunk (NC chunks); rows are visited in ascending order, 8 at a
 // time with their loads in flight together.
-template <int WMAX, int NC, bool CACHE = false>
+// Shared-memory staging of slab rows by cp.async (16 bytes per lane per
+// row chunk, each lane later reading back only what it copied itself).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// STG > 0: each batch reads 8 rows into registers and STG more into the
+// warp's staging rows in shared memory (stage, STG x P floats), so that
+// 8 + STG rows are in flight per round trip; rows are still added in
+// ascending order.
+template <int WMAX, int NC, bool CACHE = false, int STG = 0>
 __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __restrict__ g,
                                                 const uint32_t (&x)[WMAX], int i, float delta, int lane,
-                                                uint32_t* __restrict__ rows, float* __restrict__ cache = nullptr)
+                                                uint32_t* __restrict__ rows, float* __restrict__ cache = nullptr,
+                                                float* __restrict__ stage = nullptr)
 {
     const int N = p.N, P = p.P, W = p.W;
     const float* __restrict__ slab = p.S3 + (int64_t)i * N * P;
@@ -125,6 +141,45 @@ __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __rest
 #pragma unroll
     for (int c = 0; c < NC; ++c) { acc[c][0] = 0ull; acc[c][1] = 0ull; }
     int r0 = 0;
+    if (STG > 0) {
+#pragma unroll 1
+        for (; r0 + 8 + STG <= nrows; r0 += 8 + STG) {
+#pragma unroll
+            for (int t = 0; t < STG; ++t) {
+                const uint32_t o = rows[r0 + 8 + t];
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    if (jv[c]) cp_async16(stage + t * P + 128 * c + 4 * lane, base[c] + o);
+            }
+            cp_async_commit();
+            const uint4 o0 = *reinterpret_cast<const uint4*>(rows + r0);
+            const uint4 o1 = *reinterpret_cast<const uint4*>(rows + r0 + 4);
+            const uint32_t off[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+            ulonglong2 v[8][NC];
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    v[t][c] = jv[c] ? __ldg(reinterpret_cast<const ulonglong2*>(base[c] + off[t])) : make_ulonglong2(0ull, 0ull);
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc[c][0]) : "l"(v[t][c].x));
+                    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc[c][1]) : "l"(v[t][c].y));
+                }
+            cp_async_wait_all();
+#pragma unroll
+            for (int t = 0; t < STG; ++t)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const ulonglong2 w = jv[c] ? *reinterpret_cast<const ulonglong2*>(stage + t * P + 128 * c + 4 * lane)
+                                               : make_ulonglong2(0ull, 0ull);
+                    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc[c][0]) : "l"(w.x));
+                    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc[c][1]) : "l"(w.y));
+                }
+        }
+    }
 #pragma unroll 1
     for (; r0 + 8 <= nrows; r0 += 8) {
         const uint4 o0 = *reinterpret_cast<const uint4*>(rows + r0);
@@ -300,10 +355,15 @@ __host__ __device__ constexpr int warp_region_floats(int N, int WMAX)
     return 2 * ((N + 3) & ~3) + 4 * (WMAX + 1) + 8;
 }
 
-// The same plus the last update vector (late-phase dense sweep).
+// Staging rows of the late-phase dense update (N <= 256: 27 warps of an SM
+// then fit in shared memory with them).
+__host__ __device__ constexpr int reuse_stage_rows(int WMAX) { return WMAX <= 8 ? 4 : 0; }
+
+// The same plus the last update vector and the staging rows (late-phase
+// dense sweep).
 __host__ __device__ constexpr int warp_region_floats_reuse(int N, int WMAX)
 {
-    return warp_region_floats(N, WMAX) + ((N + 3) & ~3);
+    return warp_region_floats(N, WMAX) + (1 + reuse_stage_rows(WMAX)) * ((N + 3) & ~3);
 }
 
 // The whole anneal of state b of the instance described by p, run by one
@@ -396,8 +456,8 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                         for (int j = lane; j < N; j += 32) g[j] = __fadd_rn(g[j], __fmul_rn(delta, ucache[j]));
                     } else {
                         __syncwarp();
-                        nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1), true>(p, g, x, fi, delta, lane,
-                                                                                      rows, ucache);
+                        nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1), true, reuse_stage_rows(WMAX)>(
+                            p, g, x, fi, delta, lane, rows, ucache, ucache + NPAD);
                         last_bit = fi;
                         last_comp = comp;
                     }
