@@ -372,7 +372,8 @@ def run_ours(a):
                           "int_encoded": measure_int_encoded(),
                           "learned_proposal": measure_learned(a.learned_train),
                           "tensor_train": measure_tt(),
-                          "order4_contraction": measure_tc4()}
+                          "order4_contraction": measure_tc4(),
+                          "high_order_term_list": measure_high_order()}
     if rank == 0 and not a.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(inst, betas, a.cpu_states)
         cores = host_cores()
@@ -771,6 +772,7 @@ def measure_int_encoded():
 
 
 LEARNED_FORMS = (("learned_order", dict(plain_every=4, select=0, top_frac=1.0)),
+                 ("learned_order_top_half", dict(plain_every=4, select=0, top_frac=0.5)),
                  ("learned_threshold_m1", dict(plain_every=4, select=1, threshold=-1.0)),
                  ("learned_threshold_m3", dict(plain_every=4, select=1, threshold=-3.0)))
 
@@ -963,6 +965,40 @@ def measure_tc4(N: int = 64, B: int = 4096):
     out["tensor_core_issued_tflops"] = 3 * B * N * n4 * 64 * 64 * 2 / (out["tensor_core_ms"] / 1000.0) / 1e12
     out["speedup"] = out["term_list_ms"] / out["tensor_core_ms"]
     h.close()
+    return out
+
+
+def measure_high_order(B: int = 4096, cases=((5, 32), (6, 16), (6, 24))):
+    """Energies and fields of B random states of dense order-5 and order-6
+    instances (every monomial of degree 1..k over N variables, N(0,1)) on
+    the term-list path and on the order-k tensor-core path (rows over
+    sorted (k-2)-prefixes), with the work counts of each: the tensor-core
+    epilogue adds, per state and variable m, the rows whose prefix bits are
+    all set, N * C(N, k-2) masked adds per state, against k * C(N, k)
+    incidences of the term list, which tests 32 states per mask."""
+    import math
+
+    import torch
+
+    import paper_2407_19987_gb300 as H
+    out = []
+    for k, N in cases:
+        inst = W.dense_all_degrees(60 + k, N, k, "normal")
+        h = H.Instance.from_terms(inst.idx, inst.coef, inst.N)
+        X = torch.from_numpy(W.pack_bits(W.random_states(9, B, N)).view(np.int32)).cuda()
+        times = {}
+        for name, path in (("term_list", H.PATH_TERMS), ("tensor_core", H.PATH_TENSOR_CORE)):
+            h.energy(X, path=path)
+            times[name] = statistics.median(_timed_ms(lambda: h.energy(X, path=path))[1] for _ in range(5))
+        ms = times["term_list"]
+        top = math.comb(N, k)
+        out.append({"order": k, "N": N, "monomials": int(inst.nnz), "top_degree_monomials": top,
+                    "term_list_ms": ms, "states_per_s": B / (ms / 1e3),
+                    "tensor_core_ms": times["tensor_core"], "speedup": ms / times["tensor_core"],
+                    "term_list_incidences_per_state": k * top,
+                    "tc_epilogue_masked_adds_per_state": N * math.comb(N, k - 2),
+                    "tc_mma_macs_per_state": N * math.comb(N, k - 2) * 64})
+        h.close()
     return out
 
 

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -94,7 +95,7 @@ static void free_layouts(DevLayouts& d)
 {
     void* ptrs[] = {d.tvars, d.tfix, d.fptr, d.fvars, d.ffix, d.cptr, d.chdr,
                     d.ltgt, d.lcnt, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf, d.S3limb, d.rs_a, d.rs_S2,
-                    d.C3fix, d.S2fix, d.afix, d.pair_m, d.pair_j, d.S4bf, d.S3flimb, d.fa};
+                    d.C3fix, d.S2fix, d.afix, d.pair_m, d.pair_j, d.S4bf, d.S3flimb, d.fa, d.SKbf, d.kmask, d.kmin};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d = DevLayouts{};
@@ -302,6 +303,93 @@ static int build_tc4(hobo_instance* h, const std::vector<Entry>& mono, unsigned 
     return HOBO_OK;
 }
 
+// Order-5/6 tensor-core layout (layout in DevLayouts): rows over the sorted
+// (k-2)-subsets of the variables in lexicographic order, each top-degree
+// monomial placed once per member m at row (m, its other members but the
+// largest), column = that largest member; degrees < k in a child instance
+// (which may take a tensor-core path of its own).  Left out (term-list path
+// for everything) beyond 2 GB of planes or if the planes cannot be
+// described to TMA.
+static int build_tck(hobo_instance* h, const std::vector<Entry>& mono, unsigned flags, double maxabs)
+{
+    DevLayouts& d = h->d;
+    const int N = h->N, k = h->order, pk = k - 2;
+    // sorted pk-subsets in lexicographic order, by prefix bit mask
+    std::vector<unsigned long long> masks;
+    std::vector<uint8_t> mins;
+    {
+        std::vector<int> c(pk);
+        for (int q = 0; q < pk; ++q) c[q] = q;
+        while (pk <= N) {
+            unsigned long long mk = 0;
+            for (int q = 0; q < pk; ++q) mk |= 1ull << c[q];
+            masks.push_back(mk);
+            mins.push_back((uint8_t)c[0]);
+            int q = pk - 1;
+            while (q >= 0 && c[q] == N - pk + q) --q;
+            if (q < 0) break;
+            ++c[q];
+            for (int r = q + 1; r < pk; ++r) c[r] = c[r - 1] + 1;
+        }
+    }
+    const int R = (int)masks.size();
+    const int RK = (R + 255) / 256 * 256;
+    int nsplit = 3;
+    if (h->integer && maxabs < 65536.0 && !(flags & HOBO_SPLIT3)) nsplit = 2;
+    if (!h->integer && (flags & HOBO_SPLIT2)) nsplit = 2;
+    const size_t plane = (size_t)N * RK * 64;
+    if ((double)plane * nsplit * 2.0 > 2.0e9) return HOBO_OK;
+    std::vector<Entry> lower;
+    for (auto& e : mono)
+        if (e.m.d < k) lower.push_back(e);
+    if (!lower.empty()) {
+        hobo_instance* lo = new (std::nothrow) hobo_instance();
+        if (!lo) return fail(HOBO_ERR_OOM, "host allocation failed");
+        lo->N = N;
+        lo->order = k - 1;
+        lo->device = h->device;
+        lo->num_sms = h->num_sms;
+        lo->status = h->status;
+        lo->owns_status = false;
+        const int rc = build_instance(lo, lower, flags & (HOBO_SPLIT2 | HOBO_SPLIT3));
+        if (rc != HOBO_OK) { destroy_instance(lo); return rc; }
+        h->low = lo;
+    }
+    std::unordered_map<unsigned long long, int> row_of;
+    row_of.reserve((size_t)R * 2);
+    for (int r = 0; r < R; ++r) row_of[masks[r]] = r;
+    std::vector<uint16_t> planes(plane * nsplit, 0);
+    for (auto& e : mono) {
+        if (e.m.d != k) continue;
+        uint16_t sp[3];
+        choose_split(e.c, nsplit, sp);
+        for (int a = 0; a < k; ++a) {
+            const int m = e.m.v[a];
+            // the other members, ascending (e.m.v is sorted): prefix + largest
+            unsigned long long mk = 0;
+            int l = -1, n = 0;
+            for (int b = 0; b < k; ++b) {
+                if (b == a) continue;
+                if (++n == k - 1) l = e.m.v[b];
+                else mk |= 1ull << e.m.v[b];
+            }
+            const size_t at = ((size_t)m * RK + row_of.at(mk)) * 64 + l;
+            for (int q = 0; q < nsplit; ++q) planes[q * plane + at] = sp[q];
+        }
+    }
+    masks.resize(RK, 0ull);
+    mins.resize(RK, (uint8_t)255);
+    d.nsplitK = nsplit;
+    d.RK = RK;
+    int rc;
+    if ((rc = upload(&d.SKbf, planes)) || (rc = upload(&d.kmask, masks)) || (rc = upload(&d.kmin, mins))) return rc;
+    if (make_tck_tensor_map(h) != cudaSuccess) {
+        (void)cudaGetLastError();
+        d.tmapK_ok = false;
+    }
+    return HOBO_OK;
+}
+
 // Build every layout from the folded monomial list (sorted by degree, then
 // variables) and upload it.
 static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned flags)
@@ -480,6 +568,15 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
                 if (rc4 != HOBO_OK) return rc4;
             }
         }
+        // order-5/6 tensor-core contraction when the top degree is dense
+        if ((K == 5 || K == 6) && N >= K && N <= 64 && !(flags & HOBO_FORCE_SPARSE)) {
+            double ck = 1.0;
+            for (int q = 0; q < K; ++q) ck = ck * (N - q) / (q + 1);
+            if ((flags & HOBO_FORCE_DENSE) || (ck > 0 && (double)h->terms[K] >= 0.25 * ck)) {
+                const int rck = build_tck(h, mono, flags, maxabs);
+                if (rck != HOBO_OK) return rck;
+            }
+        }
         // (3) update lists grouped by (flipped bit i, target j)
         const int KU = h->KU;
         std::vector<int32_t> cnt((size_t)N * N, 0);
@@ -637,6 +734,11 @@ int hobo::energy_dispatch(const hobo_instance* h, const uint32_t* X, int B, floa
         cudaError_t e = launch_energy_tc4(h, X, B, E, g, flip, st);
         if (e == cudaSuccess) return HOBO_OK;
         return cuda_fail(e, "order-4 tensor-core contraction");
+    }
+    if ((path == 2 || path == 0) && tck_supported(h)) {
+        cudaError_t e = launch_energy_tck(h, X, B, E, g, flip, st);
+        if (e == cudaSuccess) return HOBO_OK;
+        return cuda_fail(e, "order-5/6 tensor-core contraction");
     }
     if (path == 3) {
         cudaError_t e = launch_energy_tc(h, X, B, E, g, flip, st);

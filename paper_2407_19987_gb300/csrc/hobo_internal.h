@@ -102,6 +102,18 @@ struct DevLayouts {
     int nsplit4 = 0, R4 = 0;
     alignas(64) unsigned char tmap4[128] = {};
     bool tmap4_ok = false;
+    // order-5/6 tensor-core contraction (N <= 64, top degree dense): rows
+    // (m, P) over the sorted (k-2)-subsets P of the variables in
+    // lexicographic order, RK of them padded to 256; plane entry (m, P, l) =
+    // coefficient of P + {l} + {m} for l > max P, l and m not in P; bf16
+    // split planes [nsplitK][N][RK][64]; kmask [RK] the prefix bits, kmin [RK]
+    // the prefix's smallest member; degrees < k in the child instance.
+    uint16_t* SKbf = nullptr;
+    unsigned long long* kmask = nullptr;
+    uint8_t* kmin = nullptr;
+    int nsplitK = 0, RK = 0;
+    alignas(64) unsigned char tmapK[128] = {};
+    bool tmapK_ok = false;
 };
 
 }  // namespace hobo
@@ -172,6 +184,10 @@ cudaError_t make_tc_tensor_map(hobo_instance* h);
 cudaError_t make_tc_tensor_map_rs(hobo_instance* h);
 cudaError_t make_tc4_tensor_map(hobo_instance* h);
 bool tc4_supported(const hobo_instance* h);
+bool tck_supported(const hobo_instance* h);
+cudaError_t make_tck_tensor_map(hobo_instance* h);
+cudaError_t launch_energy_tck(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g_or_dE,
+                              bool flip_out, cudaStream_t st);
 cudaError_t launch_energy_tc4(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g_or_dE,
                               bool flip_out, cudaStream_t st);
 cudaError_t launch_energy_exact_tc(const hobo_instance* h, const uint32_t* X, int B, unsigned long long* acc,

@@ -737,6 +737,333 @@ cudaError_t launch_energy_tc4(const hobo_instance* h, const uint32_t* X, int B, 
 }
 
 // ---------------------------------------------------------------------------
+// Order-k tensor-core contraction, k = 5 or 6 (the order-4 kernel's scheme
+// with rows over sorted index prefixes).  The top-degree part of the field
+// of m is g_m = sum over (k-1)-sets T not containing m of c_{T+m} x^T.  Each
+// T is split into its k-2 smallest members P (a sorted prefix) and its
+// largest member l, so with rows (m, P) over every sorted (k-2)-subset P of
+// the variables and K = l,
+//   D[b][(m, P)] = sum_{l > max P} C[m][P][l] x_bl
+// on the tensor cores, and g_bm = sum over rows whose prefix bits are all set
+// of D (each T once: no (k-1)! repeats of a fully symmetric tensor).  The
+// energy takes the rows with min P > m only (each monomial once, at its
+// smallest member m): E_k = sum_m x_bm sum_{P > m, x^P = 1} D.  Each row's
+// prefix is a bit mask (N <= 64) and its smallest member, in tables read by
+// the epilogue.  Coefficients split into bf16 planes (hi + lo, exact for
+// integers below 2^16; hi + mid + lo otherwise), float32 accumulation.  Same
+// roles, stages and bounded waits as the order-4 kernel; items are (m,
+// 256-row chunk).
+// ---------------------------------------------------------------------------
+struct TckParams {
+    const uint32_t* X;
+    int B, N, W, RK, nsplit;
+    int T, chunks, G;
+    const unsigned long long* rmask;   // [RK] prefix bits of each row (padding rows: 0, zero planes)
+    const uint8_t* rmin;               // [RK] smallest member of the prefix
+    float* GK;        // [B][N] top-degree field parts
+    float* Epart;     // [G][128][4]
+    int* status;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+energy_tck_kernel(const __grid_constant__ CUtensorMap tmap, const TckParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr int NJK = 256;
+    const uint32_t stage_bytes = (uint32_t)NJK * 128u;
+    uint8_t* sA = smem;                          // one K block (l < 64)
+    uint8_t* sB = sA + 16384;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kTcStages * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kTcStages;
+    uint64_t* afull = bars + 2 * kTcStages;
+    uint64_t* aempty = afull + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(aempty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+    volatile int* never_set = abort_flag + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = p.N, W = p.W, B = p.B;
+    const int nchk = p.RK / NJK;                 // row chunks per m
+    const int c = blockIdx.x;
+    const int tile_c = c % p.T, chunk = c / p.T;
+    const int i0 = tile_c * N + (int)((int64_t)chunk * N / p.chunks);
+    const int i1 = tile_c * N + (int)((int64_t)(chunk + 1) * N / p.chunks);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&afull[s], 1);
+            mbar_init(&aempty[s], 4);
+        }
+        *abort_flag = 0;
+        *never_set = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    int pstage = 0;
+    uint32_t pphase = 0;
+    uint32_t armed_phase[kTcStages];
+    bool armed[kTcStages];
+    for (int s = 0; s < kTcStages; ++s) { armed[s] = false; armed_phase[s] = 0; }
+    int cstage = 0;
+    uint32_t cphase = 0;
+    int acc_mma = 0, acc_epi = 0;
+    const uint32_t idesc = idesc_bf16(kTcM, NJK);
+
+    for (int it = i0; it < i1;) {
+        const int tile = it / N;
+        const int seg_end = min(i1, (tile + 1) * N);
+        // A operand: bits l < 64 of the tile's 128 states, bf16, swizzled
+        for (int q = threadIdx.x; q < kTcM * 8; q += blockDim.x) {
+            const int r = q >> 3, ch = q & 7;
+            const int b = tile * kTcM + r;
+            const int l0 = ch * 8;
+            uint32_t byte = 0;
+            if (b < B && l0 < N) {
+                byte = (p.X[(int64_t)b * W + (l0 >> 5)] >> (l0 & 31)) & 0xFFu;
+                const int rem = N - l0;
+                if (rem < 8) byte &= (1u << rem) - 1u;
+            }
+            uint32_t wv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t lo = ((byte >> (2 * e)) & 1u) ? 0x3F80u : 0u;
+                const uint32_t hi = ((byte >> (2 * e + 1)) & 1u) ? 0x3F80u : 0u;
+                wv[e] = lo | (hi << 16);
+            }
+            uint8_t* dst = sA + (r >> 3) * 1024 + (r & 7) * 128 + ((ch ^ (r & 7)) << 4);
+            *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+
+        if (warp == 0) {
+            if (lane == 0) {
+                bool ok = true;
+                for (int j = it; j < seg_end && ok && !*abort_flag; ++j) {
+                    const int m = j % N;
+                    for (int cc = 0; cc < nchk && ok; ++cc)
+                        for (int q = 0; q < p.nsplit; ++q) {
+                            if (!mbar_wait(&empty[pstage], pphase ^ 1u, abort_flag)) {
+                                set_abort(abort_flag, p.status);
+                                ok = false;
+                                break;
+                            }
+                            mbar_expect_tx(&full[pstage], stage_bytes);
+                            tma_load_2d(sB + pstage * stage_bytes, &tmap, 0, (q * N + m) * p.RK + cc * NJK,
+                                        &full[pstage]);
+                            armed[pstage] = true;
+                            armed_phase[pstage] = pphase;
+                            if (++pstage == kTcStages) { pstage = 0; pphase ^= 1u; }
+                        }
+                }
+            }
+        } else if (warp == 1) {
+            if (lane == 0) {
+                bool ok = true;
+                for (int j = it; j < seg_end && ok && !*abort_flag; ++j) {
+                    for (int cc = 0; cc < nchk && ok; ++cc) {
+                        const int buf = acc_mma & 1;
+                        if (!mbar_wait(&aempty[buf], (((uint32_t)acc_mma >> 1) & 1u) ^ 1u, abort_flag)) {
+                            set_abort(abort_flag, p.status);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d = tmem + (uint32_t)(buf * 256);
+                        uint32_t accum = 0;
+                        for (int q = 0; q < p.nsplit; ++q) {
+                            if (!mbar_wait(&full[cstage], cphase, abort_flag)) {
+                                set_abort(abort_flag, p.status);
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint64_t ad = sw128_desc(smem_u32(sA));
+                            const uint64_t bd = sw128_desc(smem_u32(sB + cstage * stage_bytes));
+#pragma unroll
+                            for (int k = 0; k < kTcKB / 16; ++k) {
+                                tc_mma(d, ad + 2 * k, bd + 2 * k, idesc, accum);
+                                accum = 1;
+                            }
+                            tc_commit(&empty[cstage]);
+                            if (++cstage == kTcStages) { cstage = 0; cphase ^= 1u; }
+                        }
+                        if (!ok) break;
+                        tc_commit(&afull[buf]);
+                        ++acc_mma;
+                    }
+                }
+            }
+        } else {
+            const int quad = warp & 3;
+            const int r = quad * 32 + lane;
+            const int b = tile * kTcM + r;
+            unsigned long long xb = 0ull;
+            if (b < B) {
+                xb = p.X[(int64_t)b * W];
+                if (W > 1) xb |= (unsigned long long)p.X[(int64_t)b * W + 1] << 32;
+                if (N < 64) xb &= (1ull << N) - 1ull;
+            }
+            float ek = 0.f;
+            bool ok = true;
+            for (int j = it; j < seg_end && ok; ++j) {
+                const int m = j % N;
+                float g0 = 0.f, g1 = 0.f, e0 = 0.f, e1 = 0.f;
+                for (int cc = 0; cc < nchk; ++cc) {
+                    const int buf = acc_epi & 1;
+                    ok = __all_sync(0xffffffffu, mbar_wait(&afull[buf], ((uint32_t)acc_epi >> 1) & 1u, abort_flag));
+                    if (!ok) {
+                        if (lane == 0) set_abort(abort_flag, p.status);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 256);
+#pragma unroll 1
+                    for (int gq = 0; gq < 8; ++gq) {
+                        uint32_t v[32];
+                        tmem_ld32(tbase + (uint32_t)(gq * 32), v);
+                        const int row0 = cc * NJK + 32 * gq;
+                        // the 32 rows' masks and smallest members: lane t
+                        // loads row t, the warp shares them by shuffles
+                        const unsigned long long mk = __ldg(p.rmask + row0 + lane);
+                        const int mn = __ldg(p.rmin + row0 + lane);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int t = 0; t < 32; t += 2) {
+                            const unsigned long long m0 = __shfl_sync(0xffffffffu, mk, t);
+                            const unsigned long long m1 = __shfl_sync(0xffffffffu, mk, t + 1);
+                            const int n0 = __shfl_sync(0xffffffffu, mn, t);
+                            const int n1 = __shfl_sync(0xffffffffu, mn, t + 1);
+                            if ((xb & m0) == m0) {
+                                g0 = __fadd_rn(g0, __uint_as_float(v[t]));
+                                if (n0 > m) e0 = __fadd_rn(e0, __uint_as_float(v[t]));
+                            }
+                            if ((xb & m1) == m1) {
+                                g1 = __fadd_rn(g1, __uint_as_float(v[t + 1]));
+                                if (n1 > m) e1 = __fadd_rn(e1, __uint_as_float(v[t + 1]));
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&aempty[buf]);
+                    ++acc_epi;
+                }
+                if (!ok) break;
+                if ((xb >> m) & 1ull) ek = __fadd_rn(ek, __fadd_rn(e0, e1));
+                if (b < B) p.GK[(int64_t)b * N + m] = __fadd_rn(g0, g1);
+            }
+            float* dst = p.Epart + (((int64_t)c) * kTcM + r) * 4;
+            dst[0] = ek; dst[1] = 0.f; dst[2] = 0.f; dst[3] = 0.f;
+        }
+        __syncthreads();
+        it = seg_end;
+    }
+
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        for (int s = 0; s < kTcStages; ++s)
+            if (armed[s]) (void)mbar_wait(&full[s], armed_phase[s], never_set);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// E = E_low + the top-degree partials of the tile's m-chunks (in chunk
+// order); g = g_low + gK, with dE = (1 - 2 x) g when flip.
+__global__ void energy_tck_finalize(const float* __restrict__ Epart, const float* __restrict__ GK,
+                                    const uint32_t* __restrict__ X, int B, int N, int W, int T, int chunks,
+                                    int has_low, int flip, float* __restrict__ E, float* __restrict__ g)
+{
+    const int b = blockIdx.x;
+    if (b >= B) return;
+    const int t = b / kTcM, r = b % kTcM;
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int k = 0; k < chunks; ++k) s = __fadd_rn(s, Epart[((int64_t)(k * T + t) * kTcM + r) * 4]);
+        E[b] = has_low ? __fadd_rn(E[b], s) : s;
+    }
+    if (g) {
+        for (int m = threadIdx.x; m < N; m += blockDim.x) {
+            const int64_t at = (int64_t)b * N + m;
+            float v = has_low ? __fadd_rn(g[at], GK[at]) : GK[at];
+            if (flip && ((X[(int64_t)b * W + (m >> 5)] >> (m & 31)) & 1u)) v = -v;
+            g[at] = v;
+        }
+    }
+}
+
+bool tck_supported(const hobo_instance* h)
+{
+    return (h->order == 5 || h->order == 6) && h->d.SKbf && h->d.tmapK_ok && h->N <= 64;
+}
+
+cudaError_t make_tck_tensor_map(hobo_instance* h)
+{
+    const auto& d = h->d;
+    cudaError_t e = encode_planes_map(h->d.tmapK, d.SKbf, d.nsplitK, h->N, d.RK, 64, 256);
+    h->d.tmapK_ok = e == cudaSuccess;
+    return e;
+}
+
+cudaError_t launch_energy_tck(const hobo_instance* h, const uint32_t* X, int B, float* E, float* g_or_dE,
+                              bool flip_out, cudaStream_t st)
+{
+    if (!tck_supported(h)) return cudaErrorNotSupported;
+    if (B == 0) return cudaSuccess;
+    const auto& d = h->d;
+    cudaError_t e = cudaSuccess;
+    if (h->low) {
+        const int rc = energy_dispatch(h->low, X, B, E, g_or_dE, false, 0, st);
+        if (rc != HOBO_OK) return cudaErrorUnknown;
+    }
+    const int tiles = (B + kTcM - 1) / kTcM;
+    const int chunks = std::max(1, std::min(h->N, h->num_sms / tiles));
+    TckParams p{};
+    p.X = X; p.B = B; p.N = h->N; p.W = h->W; p.RK = d.RK; p.nsplit = d.nsplitK;
+    p.T = tiles; p.chunks = chunks; p.G = tiles * chunks; p.status = h->status;
+    p.rmask = d.kmask; p.rmin = d.kmin;
+    float *Epart = nullptr, *GK = nullptr;
+    e = cudaMallocAsync((void**)&Epart, sizeof(float) * (size_t)p.G * kTcM * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&GK, sizeof(float) * (size_t)B * h->N, st);
+    p.Epart = Epart;
+    p.GK = GK;
+    const size_t sm = 1024 + 16384 + (size_t)kTcStages * 256 * 128 + 256;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(energy_tck_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) {
+        const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(d.tmapK);
+        energy_tck_kernel<<<p.G, kTcThreads, sm, st>>>(*map, p);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        energy_tck_finalize<<<B, 64, 0, st>>>(Epart, GK, X, B, h->N, h->W, tiles, chunks, h->low ? 1 : 0,
+                                              flip_out ? 1 : 0, E, g_or_dE);
+        e = cudaGetLastError();
+    }
+    if (Epart) cudaFreeAsync(Epart, st);
+    if (GK) cudaFreeAsync(GK, st);
+    return e;
+}
+
+// ---------------------------------------------------------------------------
 // Exact re-score on the tensor cores.  The fixed-point cubic coefficients
 // C[m][j][l] (m < j < l) are split into rs_L signed 8-bit limbs, one bf16
 // plane each (exact), and for a tile of 128 states each item (m, q) forms
