@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--case-states", type=int, default=4096)
     ap.add_argument("--case-sweeps", type=int, default=30)
     ap.add_argument("--case-offset", type=int, default=0, help="first sweep of the schedule in the sweep case")
+    ap.add_argument("--case-instances", type=int, default=512, help="instances of the uneven batch in the batch case")
     ap.add_argument("--clocks-csv", default=None, help="also write the raw clock samples of the timed region here")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-workload measurement")
     ap.add_argument("--learned-train", type=int, default=64, help="training instances of the proposal network")
@@ -1048,9 +1049,11 @@ def run_kernel_case(a):
     two term-list energy+field contractions of 4096 random states of the
     sparse order-4 workload (N=96, 2% density).  tc4: two order-4
     tensor-core contractions of 4096 random states of a dense order-4
-    instance (N=64).  batch: the uneven batch (512 instances, 1024 states
-    each) through the graph form over --case-sweeps sweeps spread over its
-    schedule.  mlp: two tensor-core forward passes of the proposal network
+    instance (N=64).  batch: the first --case-instances instances of the
+    uneven batch (1024 states each) through the graph form over
+    --case-sweeps sweeps spread over its schedule, launch shape 8-warp CTAs
+    x 6 per SM.
+    mlp: two tensor-core forward passes of the proposal network
     (H=256) over --case-states x 256 feature rows.  sweep-chunks: the whole
     anneal's sweep kernel timed once in one launch and once as resumed
     launches of --case-sweeps sweeps each (CUDA events), with the accepted
@@ -1072,13 +1075,17 @@ def run_kernel_case(a):
         print("kernel case done: mlp")
         return 0
     if a.kernel_case == "batch":
-        insts = W.uneven_batch(4000, 512)
+        # the first --case-instances instances of the uneven batch, the
+        # batch kernel's launch shape fixed at the one the autotuner picks
+        # for the whole batch (8-warp CTAs, 6 per SM), no tuning probes
+        insts = W.uneven_batch(4000, 512)[:a.case_instances]
         T0, T1, S, B = W.SCHEDULES["uneven_batch"]
         bs = W.geometric_betas(T0, T1, S)
         idx = np.linspace(0, S - 1, a.case_sweeps).round().astype(int)
         hs = [H.Instance.from_terms(i.idx, i.coef, i.N) for i in insts]
         bt = H.Batch(hs, [B] * len(hs))
-        bt.anneal([4000 + t for t in range(len(hs))], bs[idx], mode=H.HOBO_BATCH_GRAPH)
+        bt.anneal([4000 + t for t in range(len(hs))], bs[idx], mode=H.HOBO_BATCH_GRAPH, no_autotune=True,
+                  warps_per_cta=8, ctas_per_sm=6)
         torch.cuda.synchronize()
         print("kernel case done: batch")
         return 0

@@ -94,7 +94,7 @@ static int upload(T** dst, const std::vector<T>& src)
 static void free_layouts(DevLayouts& d)
 {
     void* ptrs[] = {d.tvars, d.tfix, d.fptr, d.fvars, d.ffix, d.cptr, d.chdr,
-                    d.ltgt, d.lcnt, d.ucoef, d.uconds, d.a, d.S2, d.S3, d.S3col, d.S3bf, d.S3limb, d.rs_a, d.rs_S2,
+                    d.ltgt, d.lcnt, d.ucoef, d.uconds, d.uent, d.a, d.S2, d.S3, d.S3col, d.S3bf, d.S3limb, d.rs_a, d.rs_S2,
                     d.C3fix, d.S2fix, d.afix, d.pair_m, d.pair_j, d.S4bf, d.S3flimb, d.fa, d.SKbf, d.kmask, d.kmin};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -663,6 +663,24 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
         if ((rc = upload(&d.cptr, cptr)) || (rc = upload(&d.chdr, chdr)) || (rc = upload(&d.ltgt, ltgt)) ||
             (rc = upload(&d.lcnt, lcnt)) || (rc = upload(&d.ucoef, ec)) || (rc = upload(&d.uconds, econd)))
             return rc;
+        // packed copy: coefficient bits and up to 2 (or 6) 16-bit conditions
+        {
+            const size_t ne = ec.size();
+            const int words = KU <= 2 ? 2 : 4;
+            std::vector<uint32_t> pk(ne * words, 0u);
+            for (size_t e = 0; e < ne; ++e) {
+                uint32_t cb;
+                std::memcpy(&cb, &ec[e], 4);
+                pk[e * words] = cb;
+                for (int q = 0; q < KU; ++q)
+                    pk[e * words + 1 + q / 2] |= (uint32_t)econd[e * KU + q] << (16 * (q & 1));
+                for (int q = KU; q < 2 * (words - 1); ++q)   // unused slots: the sentinel N
+                    pk[e * words + 1 + q / 2] |= (uint32_t)N << (16 * (q & 1));
+            }
+            uint32_t* dp = nullptr;
+            if ((rc = upload(&dp, pk))) return rc;
+            d.uent = dp;
+        }
     }
     return HOBO_OK;
 }

@@ -45,6 +45,10 @@ struct DevLayouts {
     uint16_t* lcnt = nullptr;    // [C][32]
     float* ucoef = nullptr;      // [Epad]
     uint16_t* uconds = nullptr;  // [Epad][KU]
+    // the same entries packed for the tuned sweeps, one load each: KU <= 2:
+    // uint2 (coefficient bits, conditions c0 | c1 << 16); KU = 6: uint4
+    // (coefficient bits, c0 | c1 << 16, c2 | c3 << 16, c4 | c5 << 16)
+    void* uent = nullptr;
 
     // (4) dense order<=3 layout: linear a[N], symmetric pair matrix S2[N][N]
     //     and symmetric cubic tensor S3[N][N][N] (zero where indices repeat),

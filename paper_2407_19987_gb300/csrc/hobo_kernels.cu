@@ -484,7 +484,7 @@ SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
     p.coef_bytes = a.coef_bytes;
     p.write_g = a.write_g ? 1 : 0;
     p.cptr = h->d.cptr; p.chdr = h->d.chdr; p.ltgt = h->d.ltgt; p.lcnt = h->d.lcnt; p.ucoef = h->d.ucoef;
-    p.uconds = h->d.uconds; p.S2 = h->d.S2; p.S3 = h->d.S3; p.S3col = h->d.S3col;
+    p.uconds = h->d.uconds; p.uent = h->d.uent; p.S2 = h->d.S2; p.S3 = h->d.S3; p.S3col = h->d.S3col;
     return p;
 }
 

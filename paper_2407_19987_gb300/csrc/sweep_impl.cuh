@@ -37,6 +37,7 @@ struct SweepDev {
     const uint16_t* lcnt;
     const float* ucoef;
     const uint16_t* uconds;
+    const void* uent;    // packed entries (coefficient bits + conditions)
     const float* S2;     // [N][P]
     const float* S3;     // [N][N][P]
     const float* S3col;  // [N][P] column sums of each slab
@@ -254,6 +255,28 @@ __device__ __forceinline__ bool dense_comp(const uint32_t (&x)[WMAX], int N)
 // chunk; each sums, in entry order, the coefficients of its entries whose
 // conditions are all set.  The entries of a step k of all lanes are adjacent,
 // so every load of the chunk is coalesced and independent of the others.
+// Entry e of the packed update lists: its coefficient if all its
+// conditions' bits are set in bs, else 0.
+template <int KU>
+__device__ __forceinline__ float packed_entry(const SweepDev& p, const uint32_t* __restrict__ bs, int64_t e)
+{
+    uint32_t pr;
+    float cv;
+    auto bit = [&](uint32_t v) { return bs[v >> 5] >> (v & 31); };
+    if (KU <= 2) {
+        const uint2 r = __ldg(reinterpret_cast<const uint2*>(p.uent) + e);
+        cv = __uint_as_float(r.x);
+        pr = bit(r.y & 0xFFFFu);
+        if (KU == 2) pr &= bit(r.y >> 16);
+    } else {
+        const uint4 r = __ldg(reinterpret_cast<const uint4*>(p.uent) + e);
+        cv = __uint_as_float(r.x);
+        pr = bit(r.y & 0xFFFFu) & bit(r.y >> 16) & bit(r.z & 0xFFFFu) & bit(r.z >> 16) & bit(r.w & 0xFFFFu) &
+             bit(r.w >> 16);
+    }
+    return (pr & 1u) ? cv : 0.0f;
+}
+
 template <int KU>
 __device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __restrict__ g,
                                                  const uint32_t* __restrict__ bs, int i, float delta,
@@ -266,22 +289,14 @@ __device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __res
         const int K = hd.y >> 6, nrec = hd.y & 63;
         const int j = p.ltgt[32 * c + lane];
         const int cnt = p.lcnt[32 * c + lane];
-        entries += __reduce_add_sync(0xffffffffu, (unsigned)cnt);
-        const float* __restrict__ cf = p.ucoef + hd.x + lane;
-        const uint16_t* __restrict__ cd = p.uconds + ((int64_t)hd.x + lane) * KU;
+        if (p.coef_bytes) entries += __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+        const int64_t e0 = (int64_t)hd.x + lane;
         float acc = 0.0f;
 #pragma unroll 4
         for (int k = 0; k < K; ++k) {
-            if (k < cnt) {
-                const float cv = __ldg(cf + 32 * k);
-                uint32_t pr = 1u;
-#pragma unroll
-                for (int s = 0; s < KU; ++s) {
-                    const int v = __ldg(cd + (int64_t)32 * k * KU + s);
-                    pr &= bs[v >> 5] >> (v & 31);
-                }
-                if (pr & 1u) acc = __fadd_rn(acc, cv);
-            }
+            // adding the 0 of an entry whose conditions are not all set
+            // changes nothing: acc starts at +0 and is never -0
+            if (k < cnt) acc = __fadd_rn(acc, packed_entry<KU>(p, bs, e0 + 32 * k));
         }
         if (lane < nrec) g[j] = __fadd_rn(g[j], __fmul_rn(delta, acc));
     }
@@ -294,20 +309,6 @@ __device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __res
 // with their entry loads interleaved, so that a flip waits on about half as
 // many dependent round trips to L2.  A target has one record, so chunks
 // touch disjoint fields and their order does not change any sum.
-template <int KU>
-__device__ __forceinline__ float ell_entry(const SweepDev& p, const uint32_t* __restrict__ bs, int off, int k,
-                                           int lane)
-{
-    const float cv = __ldg(p.ucoef + off + 32 * k + lane);
-    uint32_t pr = 1u;
-#pragma unroll
-    for (int s = 0; s < KU; ++s) {
-        const int v = __ldg(p.uconds + ((int64_t)off + 32 * k + lane) * KU + s);
-        pr &= bs[v >> 5] >> (v & 31);
-    }
-    return (pr & 1u) ? cv : 0.0f;
-}
-
 template <int KU>
 __device__ __forceinline__ int64_t sparse_update_paired(const SweepDev& p, float* __restrict__ g,
                                                         const uint32_t* __restrict__ bs, int i, float delta,
@@ -330,13 +331,14 @@ __device__ __forceinline__ int64_t sparse_update_paired(const SweepDev& p, float
             const int cntA = p.lcnt[32 * cA + lane];
             const int jB = two ? p.ltgt[32 * cB + lane] : 0;
             const int cntB = two ? p.lcnt[32 * cB + lane] : 0;
-            entries += __reduce_add_sync(0xffffffffu, (unsigned)(cntA + cntB));
+            if (p.coef_bytes) entries += __reduce_add_sync(0xffffffffu, (unsigned)(cntA + cntB));
             float accA = 0.0f, accB = 0.0f;
             const int K = max(KA, KB);
+            const int64_t eA = (int64_t)offA + lane, eB = (int64_t)offB + lane;
 #pragma unroll 2
             for (int k = 0; k < K; ++k) {
-                const float a = k < cntA ? ell_entry<KU>(p, bs, offA, k, lane) : 0.0f;
-                const float b = k < cntB ? ell_entry<KU>(p, bs, offB, k, lane) : 0.0f;
+                const float a = k < cntA ? packed_entry<KU>(p, bs, eA + 32 * k) : 0.0f;
+                const float b = k < cntB ? packed_entry<KU>(p, bs, eB + 32 * k) : 0.0f;
                 if (k < cntA) accA = __fadd_rn(accA, a);
                 if (k < cntB) accB = __fadd_rn(accB, b);
             }
