@@ -349,6 +349,29 @@ __device__ __forceinline__ int64_t sparse_update_paired(const SweepDev& p, float
     return (int64_t)(c1 - c0) * (8 + 32 * 4) + entries * (4 + 2 * KU);
 }
 
+// The Metropolis decision of metropolis() for the active lanes of a warp
+// (all 32 lanes call it), with the exp2 evaluated only when some lane needs
+// it.  For dE > 0 the decision is settled without it in two cases: a word
+// with (w >> 8) = 0 draws u = 0, accepted iff p > 0, i.e. iff the exponent
+// t >= -125; and for t < -25, p <= 2^0.5 * (1 + 4e-7) * 2^-25 < 2^-24 <= u
+// for every other word, a rejection.  Late in a schedule almost every
+// uphill exponent is far below -25, so the warp skips the polynomial.
+__device__ __forceinline__ bool metropolis_lazy(float dE, float beta, uint32_t w, bool active)
+{
+    const float a = __fmul_rn(beta, dE);
+    const float t = fminf(-__fmul_rn(a, __uint_as_float(0x3FB8AA3Bu)), 0.0f);   // log2(e)
+    const bool up = dE > 0.0f;
+    const bool u0 = (w >> 8) == 0u;
+    const bool need = active && up && !u0 && !(t < -25.0f);
+    bool acc = !up || (u0 && t >= -125.0f);
+    if (__any_sync(0xffffffffu, need)) {
+        const float p = exp2_fixed(t);
+        const float u = __fmul_rn((float)(w >> 8), 5.9604644775390625e-8f);  // 2^-24
+        if (need) acc = u < p;
+    }
+    return active && acc;
+}
+
 // Shared-memory floats one warp needs for a state of N variables: fields,
 // bits and best bits, then the dense update's list of row offsets (read 8 at
 // a time); every part a multiple of 16 bytes.
@@ -433,7 +456,14 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 const int i = 32 * w + lane;
                 bool acc = false;
                 float dE = 0.0f;
-                if (lane >= t0 && lane < nbits) {
+                if (REUSE) {
+                    const bool active = lane >= t0 && lane < nbits;
+                    if (active) {
+                        const float gi = g[i];
+                        dE = ((cw >> lane) & 1u) ? -gi : gi;
+                    }
+                    acc = metropolis_lazy(dE, beta, rw, active);
+                } else if (lane >= t0 && lane < nbits) {
                     const float gi = g[i];
                     dE = ((cw >> lane) & 1u) ? -gi : gi;
                     acc = metropolis(dE, beta, rw);
