@@ -256,13 +256,15 @@ __device__ __forceinline__ bool dense_comp(const uint32_t (&x)[WMAX], int N)
 // conditions are all set.  The entries of a step k of all lanes are adjacent,
 // so every load of the chunk is coalesced and independent of the others.
 // Entry e of the packed update lists: its coefficient if all its
-// conditions' bits are set in bs, else 0.
+// conditions' bits are set, else 0.  bb holds the state's bits one per byte
+// (bb[N] = 1: the sentinel of unused condition slots), so a condition is
+// one shared-memory byte load.
 template <int KU>
-__device__ __forceinline__ float packed_entry(const SweepDev& p, const uint32_t* __restrict__ bs, int64_t e)
+__device__ __forceinline__ float packed_entry(const SweepDev& p, const uint8_t* __restrict__ bb, int64_t e)
 {
     uint32_t pr;
     float cv;
-    auto bit = [&](uint32_t v) { return bs[v >> 5] >> (v & 31); };
+    auto bit = [&](uint32_t v) { return (uint32_t)bb[v]; };
     if (KU <= 2) {
         const uint2 r = __ldg(reinterpret_cast<const uint2*>(p.uent) + e);
         cv = __uint_as_float(r.x);
@@ -279,7 +281,7 @@ __device__ __forceinline__ float packed_entry(const SweepDev& p, const uint32_t*
 
 template <int KU>
 __device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __restrict__ g,
-                                                 const uint32_t* __restrict__ bs, int i, float delta,
+                                                 const uint8_t* __restrict__ bb, int i, float delta,
                                                  int lane)
 {
     const int c0 = p.cptr[i], c1 = p.cptr[i + 1];
@@ -296,7 +298,7 @@ __device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __res
         for (int k = 0; k < K; ++k) {
             // adding the 0 of an entry whose conditions are not all set
             // changes nothing: acc starts at +0 and is never -0
-            if (k < cnt) acc = __fadd_rn(acc, packed_entry<KU>(p, bs, e0 + 32 * k));
+            if (k < cnt) acc = __fadd_rn(acc, packed_entry<KU>(p, bb, e0 + 32 * k));
         }
         if (lane < nrec) g[j] = __fadd_rn(g[j], __fmul_rn(delta, acc));
     }
@@ -311,7 +313,7 @@ __device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __res
 // touch disjoint fields and their order does not change any sum.
 template <int KU>
 __device__ __forceinline__ int64_t sparse_update_paired(const SweepDev& p, float* __restrict__ g,
-                                                        const uint32_t* __restrict__ bs, int i, float delta,
+                                                        const uint8_t* __restrict__ bb, int i, float delta,
                                                         int lane)
 {
     const int c0 = p.cptr[i], c1 = p.cptr[i + 1];
@@ -337,8 +339,8 @@ __device__ __forceinline__ int64_t sparse_update_paired(const SweepDev& p, float
             const int64_t eA = (int64_t)offA + lane, eB = (int64_t)offB + lane;
 #pragma unroll 2
             for (int k = 0; k < K; ++k) {
-                const float a = k < cntA ? packed_entry<KU>(p, bs, eA + 32 * k) : 0.0f;
-                const float b = k < cntB ? packed_entry<KU>(p, bs, eB + 32 * k) : 0.0f;
+                const float a = k < cntA ? packed_entry<KU>(p, bb, eA + 32 * k) : 0.0f;
+                const float b = k < cntB ? packed_entry<KU>(p, bb, eB + 32 * k) : 0.0f;
                 if (k < cntA) accA = __fadd_rn(accA, a);
                 if (k < cntB) accB = __fadd_rn(accB, b);
             }
@@ -419,12 +421,15 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
     if (p.resume) Eb = p.bestE[b];
     const int wsent = N >> 5;
     const uint32_t sent = 1u << (N & 31);
+    // sparse: the bits one per byte in the (dense-only) row-list area
+    uint8_t* bb = reinterpret_cast<uint8_t*>(rows);
     if (!DENSE) {
         for (int k = lane; k <= W; k += 32) {
             uint32_t v = (k < W) ? sel_word(x, k) : 0u;
             if (k == wsent) v |= sent;
             bs[k] = v;
         }
+        for (int v = lane; v <= N; v += 32) bb[v] = v == N ? 1u : (uint8_t)((sel_word(x, v >> 5) >> (v & 31)) & 1u);
     }
     __syncwarp();
 
@@ -496,10 +501,13 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 } else if (DENSE) {
                     nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1)>(p, g, x, fi, delta, lane, rows);
                 } else {
-                    if (lane == 0) bs[w] = cw | (w == wsent ? sent : 0u);
+                    if (lane == 0) {
+                        bs[w] = cw | (w == wsent ? sent : 0u);
+                        bb[fi] = (uint8_t)((cw >> f) & 1u);
+                    }
                     __syncwarp();
-                    nbytes += PAIRED ? sparse_update_paired<KU>(p, g, bs, fi, delta, lane)
-                                      : sparse_update<KU>(p, g, bs, fi, delta, lane);
+                    nbytes += PAIRED ? sparse_update_paired<KU>(p, g, bb, fi, delta, lane)
+                                      : sparse_update<KU>(p, g, bb, fi, delta, lane);
                 }
                 __syncwarp();
                 t0 = f + 1;
@@ -684,12 +692,15 @@ __device__ __forceinline__ void anneal_state_learned(const SweepDev& p, const Le
     if (p.resume) Eb = p.bestE[b];
     const int wsent = N >> 5;
     const uint32_t sent = 1u << (N & 31);
+    // sparse: the bits one per byte in the (dense-only) row-list area
+    uint8_t* bb = reinterpret_cast<uint8_t*>(rows);
     if (!DENSE) {
         for (int k = lane; k <= W; k += 32) {
             uint32_t v = (k < W) ? sel_word(x, k) : 0u;
             if (k == wsent) v |= sent;
             bs[k] = v;
         }
+        for (int v = lane; v <= N; v += 32) bb[v] = v == N ? 1u : (uint8_t)((sel_word(x, v >> 5) >> (v & 31)) & 1u);
     }
     __syncwarp();
 
@@ -789,9 +800,12 @@ __device__ __forceinline__ void anneal_state_learned(const SweepDev& p, const Le
                 if (DENSE) {
                     nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1)>(p, g, x, fi, delta, lane, rows);
                 } else {
-                    if (lane == 0) bs[fw] = sel_word(x, fw) | (fw == wsent ? sent : 0u);
+                    if (lane == 0) {
+                        bs[fw] = sel_word(x, fw) | (fw == wsent ? sent : 0u);
+                        bb[fi] = (uint8_t)((sel_word(x, fw) >> (fi & 31)) & 1u);
+                    }
                     __syncwarp();
-                    nbytes += sparse_update<KU>(p, g, bs, fi, delta, lane);
+                    nbytes += sparse_update<KU>(p, g, bb, fi, delta, lane);
                 }
                 __syncwarp();
                 t0 = f + 1;
