@@ -305,51 +305,6 @@ __device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __res
     return (int64_t)(c1 - c0) * (8 + 32 * 4) + entries * (4 + 2 * KU);
 }
 
-// The same update for the batch kernel, whose instances have many short
-// chunks per bit.  The chunk headers of the bit are fetched together (lane
-// q holds header q and shuffles it out), and chunks are taken two at a time
-// with their entry loads interleaved, so that a flip waits on about half as
-// many dependent round trips to L2.  A target has one record, so chunks
-// touch disjoint fields and their order does not change any sum.
-template <int KU>
-__device__ __forceinline__ int64_t sparse_update_paired(const SweepDev& p, float* __restrict__ g,
-                                                        const uint8_t* __restrict__ bb, int i, float delta,
-                                                        int lane)
-{
-    const int c0 = p.cptr[i], c1 = p.cptr[i + 1];
-    int64_t entries = 0;
-    for (int cb = c0; cb < c1; cb += 32) {
-        const int nc = min(32, c1 - cb);
-        const int2 myhd = lane < nc ? p.chdr[cb + lane] : make_int2(0, 0);
-        for (int q = 0; q < nc; q += 2) {
-            const bool two = q + 1 < nc;
-            const int offA = __shfl_sync(0xffffffffu, myhd.x, q);
-            const int hyA = __shfl_sync(0xffffffffu, myhd.y, q);
-            const int offB = __shfl_sync(0xffffffffu, myhd.x, two ? q + 1 : q);
-            const int hyB = two ? __shfl_sync(0xffffffffu, myhd.y, q + 1) : 0;
-            const int cA = cb + q, cB = cb + q + 1;
-            const int KA = hyA >> 6, nA = hyA & 63, KB = hyB >> 6, nB = hyB & 63;
-            const int jA = p.ltgt[32 * cA + lane];
-            const int cntA = p.lcnt[32 * cA + lane];
-            const int jB = two ? p.ltgt[32 * cB + lane] : 0;
-            const int cntB = two ? p.lcnt[32 * cB + lane] : 0;
-            if (p.coef_bytes) entries += __reduce_add_sync(0xffffffffu, (unsigned)(cntA + cntB));
-            float accA = 0.0f, accB = 0.0f;
-            const int K = max(KA, KB);
-            const int64_t eA = (int64_t)offA + lane, eB = (int64_t)offB + lane;
-#pragma unroll 2
-            for (int k = 0; k < K; ++k) {
-                const float a = k < cntA ? packed_entry<KU>(p, bb, eA + 32 * k) : 0.0f;
-                const float b = k < cntB ? packed_entry<KU>(p, bb, eB + 32 * k) : 0.0f;
-                if (k < cntA) accA = __fadd_rn(accA, a);
-                if (k < cntB) accB = __fadd_rn(accB, b);
-            }
-            if (lane < nA) g[jA] = __fadd_rn(g[jA], __fmul_rn(delta, accA));
-            if (two && lane < nB) g[jB] = __fadd_rn(g[jB], __fmul_rn(delta, accB));
-        }
-    }
-    return (int64_t)(c1 - c0) * (8 + 32 * 4) + entries * (4 + 2 * KU);
-}
 
 // The Metropolis decision of metropolis() for the active lanes of a warp
 // (all 32 lanes call it), with the exp2 evaluated only when some lane needs
@@ -395,7 +350,7 @@ __host__ __device__ constexpr int warp_region_floats_reuse(int N, int WMAX)
 
 // The whole anneal of state b of the instance described by p, run by one
 // warp whose shared-memory region starts at g.
-template <int WMAX, bool DENSE, int KU, bool PAIRED = false, bool REUSE = false>
+template <int WMAX, bool DENSE, int KU, bool REUSE = false>
 __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g, int lane)
 {
     const int N = p.N, W = p.W;
@@ -506,8 +461,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                         bb[fi] = (uint8_t)((cw >> f) & 1u);
                     }
                     __syncwarp();
-                    nbytes += PAIRED ? sparse_update_paired<KU>(p, g, bb, fi, delta, lane)
-                                      : sparse_update<KU>(p, g, bb, fi, delta, lane);
+                    nbytes += sparse_update<KU>(p, g, bb, fi, delta, lane);
                 }
                 __syncwarp();
                 t0 = f + 1;
@@ -540,17 +494,18 @@ sweep_tuned_kernel(const SweepDev p)
     const int b = blockIdx.x * kTunedWarps + warp;       // state of this warp
     if (b >= p.B) return;                                // warp-uniform; no block barriers below
     const int rf = REUSE ? warp_region_floats_reuse(p.N, WMAX) : warp_region_floats(p.N, WMAX);
-    anneal_state<WMAX, DENSE, KU, false, REUSE>(p, b, sm + (size_t)warp * rf, lane);
+    anneal_state<WMAX, DENSE, KU, REUSE>(p, b, sm + (size_t)warp * rf, lane);
 }
 
 // Batched form: a persistent grid whose warps take (instance, state) work
 // items from a queue (items sorted by decreasing cost) until it is empty.
 // Every item is annealed exactly as the per-instance kernel would.  The
-// sparse update is bound by dependent L2 round trips, so sparse groups of up
-// to 256 variables ask for 6 resident 8-warp CTAs per SM (42 registers a
-// thread, 48 warps): uneven batch 2.25 -> 2.17 s; 8 CTAs spilled (2.75 s).
+// sparse update is bound by instruction issue and dependent L2 round trips,
+// so sparse groups of up to 256 variables ask for 7 resident 8-warp CTAs
+// per SM (40 registers a thread, some spilled; 56 warps): uneven batch
+// 1.85 -> 1.70 s against 6 CTAs, no faster with 8.
 template <bool DENSE, int WMAX>
-__host__ __device__ constexpr int batch_min_blocks() { return (!DENSE && WMAX <= 8) ? 6 : 1; }
+__host__ __device__ constexpr int batch_min_blocks() { return (!DENSE && WMAX <= 8) ? 7 : 1; }
 
 template <int WMAX, bool DENSE, int KU>
 __global__ void __launch_bounds__(256, batch_min_blocks<DENSE, WMAX>())
@@ -566,7 +521,7 @@ sweep_batch_kernel(const SweepDev* __restrict__ descs, const int2* __restrict__ 
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems) break;
         const int2 it = items[item];
-        anneal_state<WMAX, DENSE, KU, true>(descs[it.x], it.y, region, lane);
+        anneal_state<WMAX, DENSE, KU>(descs[it.x], it.y, region, lane);
         __syncwarp();
     }
 }
