@@ -306,27 +306,76 @@ __device__ __forceinline__ int64_t sparse_update(const SweepDev& p, float* __res
 }
 
 
+// Lane t's draw for word w of a group of four words whose Philox blocks the
+// warp computed together (lane L holds block 8 * (w0 + L / 8) + L % 8): the
+// draw of bit i = 32w + t is word (i % 4) of block i / 4, held by lane
+// 8 * (w - w0) + t / 4.
+__device__ __forceinline__ uint32_t lane_draw(const u32x4& r4, int w, int lane)
+{
+    const int src = 8 * (w & 3) + (lane >> 2);
+    const uint32_t ra = __shfl_sync(0xffffffffu, r4.a, src);
+    const uint32_t rb = __shfl_sync(0xffffffffu, r4.b, src);
+    const uint32_t rc = __shfl_sync(0xffffffffu, r4.c, src);
+    const uint32_t rd = __shfl_sync(0xffffffffu, r4.d, src);
+    const int e = lane & 3;
+    return e == 0 ? ra : (e == 1 ? rb : (e == 2 ? rc : rd));
+}
+
+// True when some draw of a group's blocks is u = 0 (top 24 bits zero);
+// warp-uniform.
+__device__ __forceinline__ bool group_has_zero_draw(const u32x4& r4)
+{
+    const bool z = ((r4.a >> 8) == 0u) | ((r4.b >> 8) == 0u) | ((r4.c >> 8) == 0u) | ((r4.d >> 8) == 0u);
+    return __any_sync(0xffffffffu, z) != 0;
+}
+
 // The Metropolis decision of metropolis() for the active lanes of a warp
-// (all 32 lanes call it), with the exp2 evaluated only when some lane needs
-// it.  For dE > 0 the decision is settled without it in two cases: a word
-// with (w >> 8) = 0 draws u = 0, accepted iff p > 0, i.e. iff the exponent
-// t >= -125; and for t < -25, p <= 2^0.5 * (1 + 4e-7) * 2^-25 < 2^-24 <= u
-// for every other word, a rejection.  Late in a schedule almost every
-// uphill exponent is far below -25, so the warp skips the polynomial.
-__device__ __forceinline__ bool metropolis_lazy(float dE, float beta, uint32_t w, bool active)
+// (all 32 lanes call it), evaluating only what some lane needs.  Downhill
+// moves (dE <= 0) are accepted without a draw.  For dE > 0 the decision is
+// settled without the exp2 in two cases: a word with (w >> 8) = 0 draws
+// u = 0, accepted iff p > 0, i.e. iff the exponent t >= -125; and for
+// t < -25, p <= 2^0.5 * (1 + 4e-7) * 2^-25 < 2^-24 <= u for every other
+// word, a rejection.  So when the group has no zero draw (gz false) and no
+// active uphill lane has t >= -25, every decision is known without the
+// lanes' draws, and the shuffles that fetch them are skipped; otherwise the
+// draws are fetched once per word (rw, have_rw) and the exp2 is evaluated
+// when some lane needs it.  Late in a schedule almost every uphill exponent
+// is far below -25.  cand: the lane is active and its move is not frozen
+// (frozen_uphill).
+__device__ __forceinline__ bool metropolis_lazy(float dE, float beta, bool active, bool gz, const u32x4& r4,
+                                                int w, int lane, uint32_t& rw, bool& have_rw, bool& cand)
 {
     const float a = __fmul_rn(beta, dE);
     const float t = fminf(-__fmul_rn(a, __uint_as_float(0x3FB8AA3Bu)), 0.0f);   // log2(e)
     const bool up = dE > 0.0f;
-    const bool u0 = (w >> 8) == 0u;
-    const bool need = active && up && !u0 && !(t < -25.0f);
-    bool acc = !up || (u0 && t >= -125.0f);
-    if (__any_sync(0xffffffffu, need)) {
-        const float p = exp2_fixed(t);
-        const float u = __fmul_rn((float)(w >> 8), 5.9604644775390625e-8f);  // 2^-24
-        if (need) acc = u < p;
+    cand = active && !(up && t < -125.0f);
+    bool need = active && up && !(t < -25.0f);
+    bool acc = !up;
+    if (gz || __any_sync(0xffffffffu, need)) {
+        if (!have_rw) {
+            rw = lane_draw(r4, w, lane);
+            have_rw = true;
+        }
+        const bool u0 = (rw >> 8) == 0u;
+        acc = !up || (u0 && t >= -125.0f);
+        need = need && !u0;
+        if (__any_sync(0xffffffffu, need)) {
+            const float p = exp2_fixed(t);
+            const float u = __fmul_rn((float)(rw >> 8), 5.9604644775390625e-8f);  // 2^-24
+            if (need) acc = u < p;
+        }
     }
     return active && acc;
+}
+
+// An uphill move whose exponent t is below -125: p = 0, rejected whatever
+// the draw.  t is non-increasing in beta (both roundings are monotone), so
+// with the field unchanged it stays so at any larger beta.
+__device__ __forceinline__ bool frozen_uphill(float dE, float beta)
+{
+    const float a = __fmul_rn(beta, dE);
+    const float t = fminf(-__fmul_rn(a, __uint_as_float(0x3FB8AA3Bu)), 0.0f);
+    return dE > 0.0f && t < -125.0f;
 }
 
 // Shared-memory floats one warp needs for a state of N variables: fields,
@@ -336,6 +385,10 @@ __host__ __device__ constexpr int warp_region_floats(int N, int WMAX)
 {
     return 2 * ((N + 3) & ~3) + 4 * (WMAX + 1) + 8;
 }
+
+// Longest candidate list the late-phase dense sweep walks instead of
+// visiting every bit, in steps of 32 entries.
+constexpr int kCandMaxSteps = 3;
 
 // Staging rows of the late-phase dense update (N <= 256: 27 warps of an SM
 // then fit in shared memory with them).
@@ -385,45 +438,39 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
             bs[k] = v;
         }
         for (int v = lane; v <= N; v += 32) bb[v] = v == N ? 1u : (uint8_t)((sel_word(x, v >> 5) >> (v & 31)) & 1u);
+    } else {
+        // dense: bs holds the words without a sentinel (a word is read from
+        // there once per visit instead of selected out of the registers)
+        for (int k = lane; k < W; k += 32) bs[k] = sel_word(x, k);
     }
     __syncwarp();
 
     long long nacc = 0;
     int64_t nbytes = 0;
+    float beta_next = p.sweeps > 0 ? __ldg(p.beta) : 0.0f;     // loaded one sweep ahead
+    if constexpr (!REUSE) {
     for (int s = 0; s < p.sweeps; ++s) {
-        const float beta = __ldg(p.beta + s);
+        const float beta = beta_next;
+        if (s + 1 < p.sweeps) beta_next = __ldg(p.beta + s + 1);
         const uint32_t sw = (uint32_t)(p.sweep0 + s);
         u32x4 r4 = {0u, 0u, 0u, 0u};
         for (int w = 0; w < W; ++w) {
-            uint32_t cw = sel_word(x, w);
+            // the word as it stands (the copy in bs, a sentinel bit masked)
+            uint32_t cw = bs[w] & ((!DENSE && w == wsent) ? ~sent : ~0u);
             const int nbits = min(32, N - 32 * w);
             // The draw of bit i = 32w + t is word (i % 4) of the Philox block
             // with counter (i / 4, s, b, 0).  Every fourth word, lane L
-            // computes block 8 * (w + L / 8) + L % 8, covering words w..w+3;
-            // lane t of word w' then takes its block from lane
-            // 8 * (w' - w0) + t / 4.
+            // computes block 8 * (w + L / 8) + L % 8, covering words w..w+3
+            // (lane_draw picks a lane's draw out of them).
             if ((w & 3) == 0)
                 r4 = philox10((uint32_t)(8 * w + lane), sw, p.state0 + (uint32_t)b, kStreamMetropolis, p.k0, p.k1);
-            const int src = 8 * (w & 3) + (lane >> 2);
-            const uint32_t ra = __shfl_sync(0xffffffffu, r4.a, src);
-            const uint32_t rb = __shfl_sync(0xffffffffu, r4.b, src);
-            const uint32_t rc = __shfl_sync(0xffffffffu, r4.c, src);
-            const uint32_t rd = __shfl_sync(0xffffffffu, r4.d, src);
-            const int e = lane & 3;
-            const uint32_t rw = e == 0 ? ra : (e == 1 ? rb : (e == 2 ? rc : rd));
+            const uint32_t rw = lane_draw(r4, w, lane);
             int t0 = 0;
             while (true) {
                 const int i = 32 * w + lane;
                 bool acc = false;
                 float dE = 0.0f;
-                if (REUSE) {
-                    const bool active = lane >= t0 && lane < nbits;
-                    if (active) {
-                        const float gi = g[i];
-                        dE = ((cw >> lane) & 1u) ? -gi : gi;
-                    }
-                    acc = metropolis_lazy(dE, beta, rw, active);
-                } else if (lane >= t0 && lane < nbits) {
+                if (lane >= t0 && lane < nbits) {
                     const float gi = g[i];
                     dE = ((cw >> lane) & 1u) ? -gi : gi;
                     acc = metropolis(dE, beta, rw);
@@ -437,23 +484,13 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 E = __fadd_rn(E, dEf);
                 ++nacc;
                 set_word(x, w, cw);
+                if (DENSE && lane == 0) bs[w] = cw;      // read again after the warp's next __syncwarp
                 if (E < Eb) {
                     Eb = E;
                     for (int k = lane; k < W; k += 32) bxs[k] = sel_word(x, k);
                 }
                 const int fi = 32 * w + f;
-                if (DENSE && REUSE) {
-                    const bool comp = dense_comp(x, N);
-                    if (fi == last_bit && comp == last_comp) {
-                        for (int j = lane; j < N; j += 32) g[j] = __fadd_rn(g[j], __fmul_rn(delta, ucache[j]));
-                    } else {
-                        __syncwarp();
-                        nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1), true, reuse_stage_rows(WMAX)>(
-                            p, g, x, fi, delta, lane, rows, ucache, ucache + NPAD);
-                        last_bit = fi;
-                        last_comp = comp;
-                    }
-                } else if (DENSE) {
+                if (DENSE) {
                     nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1)>(p, g, x, fi, delta, lane, rows);
                 } else {
                     if (lane == 0) {
@@ -467,8 +504,183 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 t0 = f + 1;
                 if (t0 >= nbits) break;
             }
-            set_word(x, w, cw);
         }
+    }
+    } else {
+    // Late-phase dense sweep.  With the fields fixed, a bit that
+    // frozen_uphill finds frozen at some beta is rejected at every larger
+    // beta whatever its draw.  The state keeps a candidate list, rows[0, nc):
+    // in ascending order, every bit not frozen under the current fields at
+    // beta_list.  A sweep at beta >= beta_list with a short list (at most
+    // kCandMaxSteps steps of 32) visits only the listed bits: lane k
+    // evaluates entry pos + k with its own Philox block, the first accepted
+    // entry is applied, the list is rebuilt over all bits from the new
+    // fields (cand_rebuild) and the walk goes on after that bit.  Other
+    // sweeps visit every bit, word by word, recording the list when nothing
+    // flips; when something flipped and the bits scanned after the last flip
+    // were mostly frozen, the list is rebuilt at the end.  The decisions are
+    // those of visiting every bit.  (rows also holds the update's row list:
+    // a rebuild follows every update made while a list is kept.)
+    static_assert(DENSE, "the late-phase sweep is the dense layout's");
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t st = p.state0 + (uint32_t)b;
+    const int ncmax = kCandMaxSteps * 32 < N ? kCandMaxSteps * 32 : N;
+    int nc = -1;                       // candidates in rows[0, nc); -1: no valid list
+    float beta_list = 0.0f;            // the beta the list was made or last pruned at
+    // The list for the current fields at beta bt; returns how many entries
+    // are <= bit (32 fw + f) (the walk's next position).
+    auto cand_rebuild = [&](float bt, int fw, int f) -> int {
+        int base = 0, at = 0;
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) {
+            if (k >= W) break;
+            const int nbits = min(32, N - 32 * k);
+            const bool active = lane < nbits;
+            const float gi = active ? g[32 * k + lane] : 0.0f;
+            const float dE = ((bs[k] >> lane) & 1u) ? -gi : gi;
+            const bool cand = active && !frozen_uphill(dE, bt);
+            const uint32_t m = __ballot_sync(0xffffffffu, cand);
+            if (cand) rows[base + __popc(m & lt)] = (uint32_t)(32 * k + lane);
+            if (k < fw) at += __popc(m);
+            else if (k == fw) at += __popc(m & (f == 31 ? ~0u : ((2u << f) - 1u)));
+            base += __popc(m);
+        }
+        __syncwarp();
+        nc = base;
+        beta_list = bt;
+        return at;
+    };
+    for (int s = 0; s < p.sweeps; ++s) {
+        const float beta = beta_next;
+        if (s + 1 < p.sweeps) beta_next = __ldg(p.beta + s + 1);
+        const uint32_t sw = (uint32_t)(p.sweep0 + s);
+        if (!(beta >= beta_list)) nc = -1;
+        const bool cmode = nc >= 0 && nc <= ncmax;     // walk the list this sweep
+        int pos = 0, kept = 0;                          // list walk: next entry, entries kept
+        int w = 0, t0 = 0;                              // word scan: next bit
+        bool flipped = false;
+        int ncb = 0, nscan = 0;        // word scan: candidates recorded, bits scanned since the last flip
+        int r4g = -1;                  // group whose Philox blocks r4 holds
+        u32x4 r4 = {0u, 0u, 0u, 0u};
+        bool gz = true;
+        int rww = -1;                  // word whose draws rw holds
+        uint32_t rw = 0u;
+        while (true) {
+            int fw, f;                 // the accepted bit (word, bit)
+            float dEf;
+            if (cmode) {
+                if (pos >= nc) break;
+                const int k = pos + lane;
+                const bool act = k < nc;
+                const int c = act ? (int)rows[k] : 0;
+                float dE = 0.0f;
+                bool acc = false, keep = false;
+                if (act) {
+                    const float gi = g[c];
+                    dE = ((bs[c >> 5] >> (c & 31)) & 1u) ? -gi : gi;
+                    const u32x4 r = philox10((uint32_t)(c >> 2), sw, st, kStreamMetropolis, p.k0, p.k1);
+                    const int e = c & 3;
+                    acc = metropolis(dE, beta, e == 0 ? r.a : (e == 1 ? r.b : (e == 2 ? r.c : r.d)));
+                    keep = !frozen_uphill(dE, beta);
+                }
+                const uint32_t m = __ballot_sync(0xffffffffu, acc);
+                if (m == 0u) {
+                    // prune: entries now frozen leave the list
+                    const uint32_t km = __ballot_sync(0xffffffffu, keep);
+                    __syncwarp();
+                    if (keep) rows[kept + __popc(km & lt)] = (uint32_t)c;   // at or below its own slot
+                    kept += __popc(km);
+                    pos += 32;
+                    __syncwarp();
+                    continue;
+                }
+                const int l = __ffs(m) - 1;
+                const int cf = __shfl_sync(0xffffffffu, c, l);
+                dEf = __shfl_sync(0xffffffffu, dE, l);
+                fw = cf >> 5;
+                f = cf & 31;
+            } else {
+                if (w >= W) break;
+                const uint32_t cw = bs[w];
+                const int nbits = min(32, N - 32 * w);
+                if ((w >> 2) != r4g) {
+                    r4g = w >> 2;
+                    r4 = philox10((uint32_t)(32 * r4g + lane), sw, st, kStreamMetropolis, p.k0, p.k1);
+                    gz = group_has_zero_draw(r4);
+                }
+                const bool active = lane >= t0 && lane < nbits;
+                float dE = 0.0f;
+                if (active) {
+                    const float gi = g[32 * w + lane];
+                    dE = ((cw >> lane) & 1u) ? -gi : gi;
+                }
+                bool have_rw = rww == w, cand;
+                const bool acc = metropolis_lazy(dE, beta, active, gz, r4, w, lane, rw, have_rw, cand);
+                if (have_rw) rww = w;
+                const uint32_t m = __ballot_sync(0xffffffffu, acc);
+                if (m == 0u) {
+                    const uint32_t cm = __ballot_sync(0xffffffffu, cand);
+                    if (!flipped && cand) rows[ncb + __popc(cm & lt)] = (uint32_t)(32 * w + lane);
+                    ncb += __popc(cm);
+                    nscan += nbits - t0;
+                    ++w;
+                    t0 = 0;
+                    continue;
+                }
+                fw = w;
+                f = __ffs(m) - 1;
+                dEf = __shfl_sync(0xffffffffu, dE, f);
+            }
+            // apply the flip of bit 32 fw + f
+            const uint32_t cw = bs[fw] ^ (1u << f);
+            const float delta = ((cw >> f) & 1u) ? 1.0f : -1.0f;   // +1: the bit went 0 -> 1
+            E = __fadd_rn(E, dEf);
+            ++nacc;
+            set_word(x, fw, cw);
+            if (E < Eb) {
+                Eb = E;
+                for (int k = lane; k < W; k += 32) bxs[k] = sel_word(x, k);
+            }
+            const int fi = 32 * fw + f;
+            const bool comp = dense_comp(x, N);
+            __syncwarp();
+            if (lane == 0) bs[fw] = cw;            // read again after the __syncwarp below
+            if (fi == last_bit && comp == last_comp) {
+                for (int j = lane; j < N; j += 32) g[j] = __fadd_rn(g[j], __fmul_rn(delta, ucache[j]));
+            } else {
+                nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1), true, reuse_stage_rows(WMAX)>(
+                    p, g, x, fi, delta, lane, rows, ucache, ucache + NPAD);
+                last_bit = fi;
+                last_comp = comp;
+            }
+            __syncwarp();
+            flipped = true;
+            if (cmode) {
+                pos = cand_rebuild(beta, fw, f);
+                kept = pos;
+            } else {
+                ncb = 0;
+                nscan = 0;
+                w = fw;
+                t0 = f + 1;
+                if (t0 >= min(32, N - 32 * w)) {
+                    ++w;
+                    t0 = 0;
+                }
+            }
+        }
+        if (cmode) {
+            nc = kept;
+            beta_list = beta;
+        } else if (!flipped) {
+            nc = ncb;
+            beta_list = beta;
+        } else if (4 * ncb <= nscan + 32) {
+            cand_rebuild(beta, -1, 0);
+        } else {
+            nc = -1;
+        }
+    }
     }
 
     for (int k = lane; k < W; k += 32) {

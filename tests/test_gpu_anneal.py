@@ -54,6 +54,54 @@ def test_anneal_integer_matches_oracle(name, maker, flags, B, sched, mode):
     h.close()
 
 
+def _reheat(T0, T1, S):
+    """Two geometric legs, the second starting hotter than the first ends."""
+    return np.concatenate([W.geometric_betas(T0, T1, S // 2), W.geometric_betas(T0 / 10, T1, S - S // 2)])
+
+
+LATE_CASES = [
+    # long dense anneals: after the first tenth of the sweeps the dense sweep
+    # visits only the bits it did not find frozen in the last sweep without
+    # flips; these schedules give many such sweeps with more than 32
+    # candidates, sweeps where every bit is frozen, and flips found among
+    # the candidates (then every later bit of the sweep is visited)
+    ("dense_int_N64_cold", lambda: W.random_sparse(40, 64, 3, 0.5, "int"), 4, 32,
+     lambda: W.geometric_betas(30.0, 0.05, 300)),
+    ("dense_int_N64_warm_end", lambda: W.random_sparse(40, 64, 3, 0.5, "int"), 4, 32,
+     lambda: W.geometric_betas(100.0, 0.3, 300)),
+    # beta falls at the second leg: the frozen bits must be visited again
+    ("dense_int_N64_reheat", lambda: W.random_sparse(40, 64, 3, 0.5, "int"), 4, 32, lambda: _reheat(30.0, 0.05, 300)),
+    ("tiny_dense_long", lambda: W.tiny_dense(1), 0, 64, lambda: W.geometric_betas(5.0, 0.02, 400)),
+    # ten words per state (N = 300)
+    ("dense_int_N300", lambda: W.random_sparse(61, 300, 3, 0.3, "int", imax=2), 4, 8,
+     lambda: W.geometric_betas(200.0, 0.5, 120)),
+]
+
+
+@pytest.mark.parametrize("name,maker,flags,B,sched", LATE_CASES, ids=[c[0] for c in LATE_CASES])
+def test_long_dense_anneal_matches_oracle(name, maker, flags, B, sched):
+    inst = maker()
+    betas = sched()
+    h = gpuh.make(inst, flags)
+    r = _run(h, 77, B, betas, TUNED)
+    ref = O.anneal(inst, 77, B, betas)
+    _compare_oracle(inst, r, ref, inst.N)
+    h.close()
+
+
+@pytest.mark.parametrize("sched", [lambda: W.geometric_betas(10.0, 0.01, 400), lambda: _reheat(10.0, 0.01, 400)],
+                         ids=["geometric", "reheat"])
+def test_long_dense_float_anneal_tuned_equals_plain(sched):
+    inst = W.dense_float(52, 96)
+    betas = sched()
+    h = gpuh.make(inst)
+    a = _run(h, 98, 32, betas, TUNED)
+    b = _run(h, 98, 32, betas, PLAIN)
+    for k in ("bestX", "X", "accepts", "bestE", "E"):
+        np.testing.assert_array_equal(a[k].cpu().numpy(), b[k].cpu().numpy())
+    h.close()
+
+
 WIDE_CASES = [
     # N = 1000: the widest sparse sweep (32 words per state, 8 bits in the last word)
     ("sparse_N1000", lambda: W.random_sparse(60, 1000, 3, 2e-5, "int"), 8, (20.0, 0.5, 4)),
