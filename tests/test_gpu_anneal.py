@@ -102,6 +102,34 @@ def test_long_dense_float_anneal_tuned_equals_plain(sched):
     h.close()
 
 
+def test_long_dense_anneal_many_states_match_oracle():
+    """A long dense anneal of more states than SMs: trajectories of the
+    integer instance follow the oracle for every state."""
+    inst = W.random_sparse(62, 72, 3, 0.3, "int", imax=2)
+    betas = W.geometric_betas(100.0, 0.1, 100)
+    h = gpuh.make(inst, 4)
+    r = _run(h, 78, 320, betas, TUNED)
+    ref = O.anneal(inst, 78, 320, betas)
+    _compare_oracle(inst, r, ref, inst.N)
+    h.close()
+
+
+@pytest.mark.parametrize("N", [128, 256])
+def test_long_dense_float_many_states_equal_plain(N):
+    """4096 states of a dense float instance (27 per SM) against the plain
+    kernel on a slice of 32 of them (their global state indices via
+    state0)."""
+    inst = W.dense_float(54, N)
+    betas = W.geometric_betas(10.0, 0.01, 300)
+    h = gpuh.make(inst)
+    a = _run(h, 97, 4096, betas, TUNED)
+    b = _run(h, 97, 32, betas, PLAIN, state0=1000)
+    for k in ("bestX", "X", "accepts", "bestE", "E"):
+        np.testing.assert_array_equal(a[k][1000:1032].cpu().numpy(), b[k].cpu().numpy())
+    h.check()
+    h.close()
+
+
 WIDE_CASES = [
     # N = 1000: the widest sparse sweep (32 words per state, 8 bits in the last word)
     ("sparse_N1000", lambda: W.random_sparse(60, 1000, 3, 2e-5, "int"), 8, (20.0, 0.5, 4)),
