@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--mode", default="tuned", choices=["tuned", "plain"])
     ap.add_argument("--cpu-states", type=int, default=8, help="oracle sample size (states)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-case", default=None, choices=["sweep", "sweep-resume", "sweep-chunks", "tc", "tc-f32acc", "fix", "fields", "tc4", "batch", "rescore",
+    ap.add_argument("--kernel-case", default=None, choices=["sweep", "sweep-resume", "sweep-chunks", "sweep-tail", "tc", "tc-f32acc", "fix", "fields", "tc4", "batch", "rescore",
                              "mlp"],
                     help="run one small case of one kernel (for profilers) and exit")
     ap.add_argument("--case-states", type=int, default=4096)
@@ -1003,6 +1003,49 @@ def measure_high_order(B: int = 4096, cases=((5, 32), (6, 16), (6, 24))):
     return out
 
 
+def sweep_tail(inst, betas, B: int, offset: int):
+    """The late sweeps [offset, end) of the anneal for all B states, against
+    the same sweeps for the states that read the most coefficient bytes,
+    each alone (B = 1, its global index as state0): how much of the late
+    launch one state's own work accounts for."""
+    import torch
+
+    import paper_2407_19987_gb300 as H
+    h = H.Instance.from_terms(inst.idx, inst.coef, inst.N)
+
+    def ev():
+        return [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+
+    r0 = h.anneal(2, B, betas[:offset], want_final=True, want_fields=True)
+    torch.cuda.synchronize()
+
+    def resume(idx=None):
+        sel = (lambda t: t.clone()) if idx is None else (lambda t: t[idx:idx + 1].clone())
+        e = ev()
+        out = h.anneal(2, B if idx is None else 1, betas[offset:], sweep0=offset, resume=True, X=sel(r0["X"]),
+                       bestX=sel(r0["bestX"]), bestE32=sel(r0["bestE32"]), E=sel(r0["E"]), g=sel(r0["g"]),
+                       state0=0 if idx is None else idx, sweep_events=e, want_accepts=True, want_bytes=True)
+        torch.cuda.synchronize()
+        return out, e[0].elapsed_time(e[1])
+
+    resume()
+    out, ms = resume()
+    acc = out["accepts"].cpu().numpy()
+    cb = out["coef_bytes"].cpu().numpy()
+    row = 4 * inst.N
+    res = {"workload": f"{WORKLOAD}, B={B}, sweeps {offset}-{len(betas)}", "all_states_ms": ms,
+           "accepts": int(acc.sum()), "states": []}
+    for i in np.argsort(-cb)[:4]:
+        o1, t1 = resume(int(i))
+        res["states"].append({"state": int(i), "alone_ms": t1, "accepts": int(acc[i]),
+                              "full_update_equivalents": float(cb[i]) / (row * inst.N / 2),
+                              "same_trajectory": int(o1["accepts"].cpu().numpy()[0]) == int(acc[i])})
+    h.check()
+    h.close()
+    print(json.dumps(res))
+    return 0
+
+
 def sweep_chunks(inst, betas, B: int, C: int):
     """Where the sweep kernel's time goes along the schedule."""
     import torch
@@ -1057,7 +1100,10 @@ def run_kernel_case(a):
     (H=256) over --case-states x 256 feature rows.  sweep-chunks: the whole
     anneal's sweep kernel timed once in one launch and once as resumed
     launches of --case-sweeps sweeps each (CUDA events), with the accepted
-    flips of each chunk; prints one JSON line."""
+    flips of each chunk; prints one JSON line.  sweep-tail: sweeps
+    [--case-offset, end) for all states against the same sweeps for the
+    four states that read the most coefficient bytes, each alone; prints
+    one JSON line."""
     import torch
 
     import paper_2407_19987_gb300 as H
@@ -1092,6 +1138,8 @@ def run_kernel_case(a):
     inst, betas, B, S = workload()
     if a.kernel_case == "sweep-chunks":
         return sweep_chunks(inst, betas, a.case_states, a.case_sweeps)
+    if a.kernel_case == "sweep-tail":
+        return sweep_tail(inst, betas, a.case_states, a.case_offset)
     if a.kernel_case == "fields":
         inst = W.sparse_order4(5000)
     elif a.kernel_case == "tc4":
