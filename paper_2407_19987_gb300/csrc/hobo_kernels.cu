@@ -485,6 +485,7 @@ SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
     p.write_g = a.write_g ? 1 : 0;
     p.cptr = h->d.cptr; p.chdr = h->d.chdr; p.ltgt = h->d.ltgt; p.lcnt = h->d.lcnt; p.ucoef = h->d.ucoef;
     p.uconds = h->d.uconds; p.uent = h->d.uent; p.S2 = h->d.S2; p.S3 = h->d.S3; p.S3col = h->d.S3col;
+    p.vcache = a.vcache;
     return p;
 }
 
@@ -513,7 +514,23 @@ cudaError_t launch_sweep_tuned(const hobo_instance* h, const SweepArgs& a, cudaS
         a2.sweeps = a.sweeps - s1;
         a2.sweep0 = a.sweep0 + s1;
         a2.resume = 1;
-        return dispatch_tuned_dense_reuse(make_dev(h, a2), st);
+        // the late launch's vector cache (layouts of up to 8 words); without
+        // it the launch computes every vector, with the same results
+        float* vc = nullptr;
+        if (h->W <= 8) {
+            const size_t bytes = sizeof(float) * (size_t)a.B * kVSlots * vcache_entry_floats((h->N + 3) & ~3);
+            if (cudaMallocAsync((void**)&vc, bytes, st) != cudaSuccess) {
+                (void)cudaGetLastError();
+                vc = nullptr;
+            }
+        }
+        a2.vcache = vc;
+        e = dispatch_tuned_dense_reuse(make_dev(h, a2), st);
+        if (vc) {
+            const cudaError_t ef = cudaFreeAsync(vc, st);
+            if (e == cudaSuccess) e = ef;
+        }
+        return e;
     }
     if (h->dense) return dispatch_tuned<true, 1>(p, st);
     if (h->KU <= 1) return dispatch_tuned<false, 1>(p, st);

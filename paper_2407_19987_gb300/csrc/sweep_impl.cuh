@@ -41,7 +41,43 @@ struct SweepDev {
     const float* S2;     // [N][P]
     const float* S3;     // [N][N][P]
     const float* S3col;  // [N][P] column sums of each slab
+    float* vcache;       // late-phase dense sweep: [B][kVSlots] vector-cache entries, or null
 };
+
+// ---------------------------------------------------------------------------
+// Vector cache of the late-phase dense sweep.  The update vector of a flip
+// of bit i is a function of i and of the state after the flip (its row list
+// and the set/clear choice are), so a state that flips i again from the
+// same state gets the same float vector.  Late in a schedule the states
+// that still flip mostly cycle through a few states; each keeps its last
+// kVSlots vectors in global memory (entry: a 64-byte header -- bit, state
+// words -- and the vector's N floats), found through 32-bit tags (a hash of
+// the bit and of the state) held one per lane in registers, and verified
+// against the stored header before use.
+constexpr int kVSlots = 8;
+
+__host__ __device__ constexpr int vcache_entry_floats(int P) { return 16 + P; }
+
+// Hash terms: the state's hash is the xor of vhash_bit(i) over its set bits.
+__device__ __forceinline__ uint32_t vhash_bit(int i)
+{
+    uint32_t v = (uint32_t)i * 0x9E3779B1u + 0x7F4A7C15u;
+    v ^= v >> 15;
+    v *= 0x2C1B3C6Du;
+    v ^= v >> 12;
+    v *= 0x297A2D39u;
+    return v ^ (v >> 15);
+}
+
+__device__ __forceinline__ uint32_t vhash_key(uint32_t h, int i)
+{
+    uint32_t v = h ^ ((uint32_t)i * 0x85EBCA6Bu + 0xC2B2AE35u);
+    v ^= v >> 16;
+    v *= 0x7FEB352Du;
+    v ^= v >> 15;
+    v *= 0x846CA68Bu;
+    return v ^ (v >> 16);
+}
 
 template <int WMAX>
 __device__ __forceinline__ uint32_t sel_word(const uint32_t (&x)[WMAX], int w)
@@ -525,6 +561,16 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t st = p.state0 + (uint32_t)b;
     const int ncmax = kCandMaxSteps * 32 < N ? kCandMaxSteps * 32 : N;
+    // vector cache: this state's entries, the state's hash (warp-uniform),
+    // lane k's tag of entry k, the valid entries and the next entry to fill
+    float* const vc = (WMAX <= 8 && p.vcache) ? p.vcache + (size_t)b * kVSlots * vcache_entry_floats(p.P) : nullptr;
+    uint32_t vh = 0u;
+    for (int k = 0; k < W; ++k)
+        if ((bs[k] >> lane) & 1u) vh ^= vhash_bit(32 * k + lane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vh ^= __shfl_xor_sync(0xffffffffu, vh, o);
+    uint32_t vtag = 0u, vmask = 0u;
+    int vfifo = 0;
     int nc = -1;                       // candidates in rows[0, nc); -1: no valid list
     float beta_list = 0.0f;            // the beta the list was made or last pruned at
     // The list for the current fields at beta bt; returns how many entries
@@ -645,11 +691,43 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
             const bool comp = dense_comp(x, N);
             __syncwarp();
             if (lane == 0) bs[fw] = cw;            // read again after the __syncwarp below
+            vh ^= vhash_bit(fi);                   // the hash of the state after the flip
             if (fi == last_bit && comp == last_comp) {
                 for (int j = lane; j < N; j += 32) g[j] = __fadd_rn(g[j], __fmul_rn(delta, ucache[j]));
             } else {
-                nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1), true, reuse_stage_rows(WMAX)>(
-                    p, g, x, fi, delta, lane, rows, ucache, ucache + NPAD);
+                bool hit = false;
+                uint32_t kh = 0u;
+                if (vc) {
+                    kh = vhash_key(vh, fi);
+                    const uint32_t m = __ballot_sync(0xffffffffu, lane < kVSlots && ((vmask >> lane) & 1u) && vtag == kh);
+                    if (m) {
+                        const float* e = vc + (size_t)(__ffs(m) - 1) * vcache_entry_floats(p.P);
+                        const uint32_t* hd = reinterpret_cast<const uint32_t*>(e);
+                        const bool bad = lane <= W && hd[lane] != (lane == 0 ? (uint32_t)fi : sel_word(x, lane - 1));
+                        if (__ballot_sync(0xffffffffu, bad) == 0u) {
+                            for (int j = lane; j < N; j += 32) {
+                                const float u = e[16 + j];
+                                g[j] = __fadd_rn(g[j], __fmul_rn(delta, u));
+                                ucache[j] = u;
+                            }
+                            nbytes += (int64_t)(16 + N) * 4;
+                            hit = true;
+                        }
+                    }
+                }
+                if (!hit) {
+                    nbytes += dense_update<WMAX, (WMAX >= 4 ? WMAX / 4 : 1), true, reuse_stage_rows(WMAX)>(
+                        p, g, x, fi, delta, lane, rows, ucache, ucache + NPAD);
+                    if (vc) {
+                        float* e = vc + (size_t)vfifo * vcache_entry_floats(p.P);
+                        __syncwarp();                  // ucache: each lane wrote its own columns
+                        for (int j = lane; j < N; j += 32) e[16 + j] = ucache[j];
+                        if (lane <= W) reinterpret_cast<uint32_t*>(e)[lane] = lane == 0 ? (uint32_t)fi : sel_word(x, lane - 1);
+                        if (lane == vfifo) vtag = kh;
+                        vmask |= 1u << vfifo;
+                        vfifo = vfifo + 1 == kVSlots ? 0 : vfifo + 1;
+                    }
+                }
                 last_bit = fi;
                 last_comp = comp;
             }
