@@ -166,6 +166,7 @@ struct SweepArgs {
     int64_t* coef_bytes = nullptr; // device [B] or null
     bool write_g = false;          // tuned: write the final fields back to g
     float* vcache = nullptr;       // late-phase dense sweep: vector cache, or null
+    int vslots = 0;                // its entries per state
 };
 
 cudaError_t launch_sweep_tuned(const hobo_instance* h, const SweepArgs& a, cudaStream_t st);

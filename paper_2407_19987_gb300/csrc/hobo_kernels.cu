@@ -486,6 +486,7 @@ SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
     p.cptr = h->d.cptr; p.chdr = h->d.chdr; p.ltgt = h->d.ltgt; p.lcnt = h->d.lcnt; p.ucoef = h->d.ucoef;
     p.uconds = h->d.uconds; p.uent = h->d.uent; p.S2 = h->d.S2; p.S3 = h->d.S3; p.S3col = h->d.S3col;
     p.vcache = a.vcache;
+    p.vslots = a.vslots;
     return p;
 }
 
@@ -497,6 +498,9 @@ SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
 // first one's states, fields and energies in global memory, so the result
 // is that of one launch bit for bit.
 constexpr int kSplitMin = 16;
+
+// Device memory the late-phase vector cache may take in one call.
+constexpr size_t kVCacheBytes = 1ull << 30;
 
 cudaError_t launch_sweep_tuned(const hobo_instance* h, const SweepArgs& a, cudaStream_t st)
 {
@@ -516,15 +520,20 @@ cudaError_t launch_sweep_tuned(const hobo_instance* h, const SweepArgs& a, cudaS
         a2.resume = 1;
         // the late launch's vector cache (layouts of up to 8 words); without
         // it the launch computes every vector, with the same results
+        // (kVSlots entries per state, fewer when that would pass kVCacheBytes)
         float* vc = nullptr;
+        int slots = 0;
         if (h->W <= 8) {
-            const size_t bytes = sizeof(float) * (size_t)a.B * kVSlots * vcache_entry_floats((h->N + 3) & ~3);
-            if (cudaMallocAsync((void**)&vc, bytes, st) != cudaSuccess) {
+            const size_t entry = sizeof(float) * (size_t)vcache_entry_floats((h->N + 3) & ~3);
+            slots = (int)std::min<size_t>(kVSlots, kVCacheBytes / std::max<size_t>(1, entry * (size_t)a.B));
+            if (slots >= 2 && cudaMallocAsync((void**)&vc, entry * (size_t)a.B * slots, st) != cudaSuccess) {
                 (void)cudaGetLastError();
                 vc = nullptr;
             }
+            if (slots < 2) vc = nullptr;
         }
         a2.vcache = vc;
+        a2.vslots = vc ? slots : 0;
         e = dispatch_tuned_dense_reuse(make_dev(h, a2), st);
         if (vc) {
             const cudaError_t ef = cudaFreeAsync(vc, st);

@@ -41,7 +41,8 @@ struct SweepDev {
     const float* S2;     // [N][P]
     const float* S3;     // [N][N][P]
     const float* S3col;  // [N][P] column sums of each slab
-    float* vcache;       // late-phase dense sweep: [B][kVSlots] vector-cache entries, or null
+    float* vcache;       // late-phase dense sweep: [B][vslots] vector-cache entries, or null
+    int vslots;          // entries per state (2..kVSlots) when vcache is set
 };
 
 // ---------------------------------------------------------------------------
@@ -50,11 +51,12 @@ struct SweepDev {
 // and the set/clear choice are), so a state that flips i again from the
 // same state gets the same float vector.  Late in a schedule the states
 // that still flip mostly cycle through a few states; each keeps its last
-// kVSlots vectors in global memory (entry: a 64-byte header -- bit, state
-// words -- and the vector's N floats), found through 32-bit tags (a hash of
-// the bit and of the state) held one per lane in registers, and verified
-// against the stored header before use.
-constexpr int kVSlots = 8;
+// vslots (at most kVSlots) vectors in global memory (entry: a 64-byte header
+// -- bit, state words -- and the vector's N floats), found through 32-bit
+// tags (a hash of the bit and of the state) held one per lane in registers,
+// and verified against the stored header before use; entries are replaced
+// first in, first out.
+constexpr int kVSlots = 32;
 
 __host__ __device__ constexpr int vcache_entry_floats(int P) { return 16 + P; }
 
@@ -563,7 +565,8 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
     const int ncmax = kCandMaxSteps * 32 < N ? kCandMaxSteps * 32 : N;
     // vector cache: this state's entries, the state's hash (warp-uniform),
     // lane k's tag of entry k, the valid entries and the next entry to fill
-    float* const vc = (WMAX <= 8 && p.vcache) ? p.vcache + (size_t)b * kVSlots * vcache_entry_floats(p.P) : nullptr;
+    float* const vc = (WMAX <= 8 && p.vcache) ? p.vcache + (size_t)b * p.vslots * vcache_entry_floats(p.P) : nullptr;
+    const int vslots = p.vslots;
     uint32_t vh = 0u;
     for (int k = 0; k < W; ++k)
         if ((bs[k] >> lane) & 1u) vh ^= vhash_bit(32 * k + lane);
@@ -699,7 +702,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 uint32_t kh = 0u;
                 if (vc) {
                     kh = vhash_key(vh, fi);
-                    const uint32_t m = __ballot_sync(0xffffffffu, lane < kVSlots && ((vmask >> lane) & 1u) && vtag == kh);
+                    const uint32_t m = __ballot_sync(0xffffffffu, lane < vslots && ((vmask >> lane) & 1u) && vtag == kh);
                     if (m) {
                         const float* e = vc + (size_t)(__ffs(m) - 1) * vcache_entry_floats(p.P);
                         const uint32_t* hd = reinterpret_cast<const uint32_t*>(e);
@@ -725,7 +728,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                         if (lane <= W) reinterpret_cast<uint32_t*>(e)[lane] = lane == 0 ? (uint32_t)fi : sel_word(x, lane - 1);
                         if (lane == vfifo) vtag = kh;
                         vmask |= 1u << vfifo;
-                        vfifo = vfifo + 1 == kVSlots ? 0 : vfifo + 1;
+                        vfifo = vfifo + 1 == vslots ? 0 : vfifo + 1;
                     }
                 }
                 last_bit = fi;
