@@ -545,9 +545,10 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
         }
     }
     } else {
-    // Late-phase dense sweep.  With the fields fixed, a bit that
+    // Late-phase sweep (dense: with the vector reuse and cache; sparse: the
+    // term-list update).  With the fields fixed, a bit that
     // frozen_uphill finds frozen at some beta is rejected at every larger
-    // beta whatever its draw.  The state keeps a candidate list, rows[0, nc):
+    // beta whatever its draw.  The state keeps a candidate list, cl[0, nc):
     // in ascending order, every bit not frozen under the current fields at
     // beta_list.  A sweep at beta >= beta_list with a short list (at most
     // kCandMaxSteps steps of 32) visits only the listed bits: lane k
@@ -559,7 +560,10 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
     // were mostly frozen, the list is rebuilt at the end.  The decisions are
     // those of visiting every bit.  (rows also holds the update's row list:
     // a rebuild follows every update made while a list is kept.)
-    static_assert(DENSE, "the late-phase sweep is the dense layout's");
+    // the list: sixteen-bit bit indices, at the start of the row-list area
+    // (dense; rebuilt after every update that overwrites it) or after the
+    // state's bytes (sparse)
+    uint16_t* const cl = DENSE ? reinterpret_cast<uint16_t*>(rows) : reinterpret_cast<uint16_t*>(bb + ((N + 16) & ~15));
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t st = p.state0 + (uint32_t)b;
     const int ncmax = kCandMaxSteps * 32 < N ? kCandMaxSteps * 32 : N;
@@ -568,13 +572,15 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
     float* const vc = (WMAX <= 8 && p.vcache) ? p.vcache + (size_t)b * p.vslots * vcache_entry_floats(p.P) : nullptr;
     const int vslots = p.vslots;
     uint32_t vh = 0u;
-    for (int k = 0; k < W; ++k)
-        if ((bs[k] >> lane) & 1u) vh ^= vhash_bit(32 * k + lane);
+    if (vc) {
+        for (int k = 0; k < W; ++k)
+            if ((bs[k] >> lane) & 1u) vh ^= vhash_bit(32 * k + lane);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vh ^= __shfl_xor_sync(0xffffffffu, vh, o);
+        for (int o = 16; o > 0; o >>= 1) vh ^= __shfl_xor_sync(0xffffffffu, vh, o);
+    }
     uint32_t vtag = 0u, vmask = 0u;
     int vfifo = 0;
-    int nc = -1;                       // candidates in rows[0, nc); -1: no valid list
+    int nc = -1;                       // candidates in cl[0, nc); -1: no valid list
     float beta_list = 0.0f;            // the beta the list was made or last pruned at
     // The list for the current fields at beta bt; returns how many entries
     // are <= bit (32 fw + f) (the walk's next position).
@@ -589,7 +595,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
             const float dE = ((bs[k] >> lane) & 1u) ? -gi : gi;
             const bool cand = active && !frozen_uphill(dE, bt);
             const uint32_t m = __ballot_sync(0xffffffffu, cand);
-            if (cand) rows[base + __popc(m & lt)] = (uint32_t)(32 * k + lane);
+            if (cand) cl[base + __popc(m & lt)] = (uint16_t)(32 * k + lane);
             if (k < fw) at += __popc(m);
             else if (k == fw) at += __popc(m & (f == 31 ? ~0u : ((2u << f) - 1u)));
             base += __popc(m);
@@ -621,7 +627,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 if (pos >= nc) break;
                 const int k = pos + lane;
                 const bool act = k < nc;
-                const int c = act ? (int)rows[k] : 0;
+                const int c = act ? (int)cl[k] : 0;
                 float dE = 0.0f;
                 bool acc = false, keep = false;
                 if (act) {
@@ -637,7 +643,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                     // prune: entries now frozen leave the list
                     const uint32_t km = __ballot_sync(0xffffffffu, keep);
                     __syncwarp();
-                    if (keep) rows[kept + __popc(km & lt)] = (uint32_t)c;   // at or below its own slot
+                    if (keep) cl[kept + __popc(km & lt)] = (uint16_t)c;   // at or below its own slot
                     kept += __popc(km);
                     pos += 32;
                     __syncwarp();
@@ -650,7 +656,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 f = cf & 31;
             } else {
                 if (w >= W) break;
-                const uint32_t cw = bs[w];
+                const uint32_t cw = bs[w] & ((!DENSE && w == wsent) ? ~sent : ~0u);
                 const int nbits = min(32, N - 32 * w);
                 if ((w >> 2) != r4g) {
                     r4g = w >> 2;
@@ -669,7 +675,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 const uint32_t m = __ballot_sync(0xffffffffu, acc);
                 if (m == 0u) {
                     const uint32_t cm = __ballot_sync(0xffffffffu, cand);
-                    if (!flipped && cand) rows[ncb + __popc(cm & lt)] = (uint32_t)(32 * w + lane);
+                    if (!flipped && cand) cl[ncb + __popc(cm & lt)] = (uint16_t)(32 * w + lane);
                     ncb += __popc(cm);
                     nscan += nbits - t0;
                     ++w;
@@ -681,7 +687,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 dEf = __shfl_sync(0xffffffffu, dE, f);
             }
             // apply the flip of bit 32 fw + f
-            const uint32_t cw = bs[fw] ^ (1u << f);
+            const uint32_t cw = (bs[fw] & ((!DENSE && fw == wsent) ? ~sent : ~0u)) ^ (1u << f);
             const float delta = ((cw >> f) & 1u) ? 1.0f : -1.0f;   // +1: the bit went 0 -> 1
             E = __fadd_rn(E, dEf);
             ++nacc;
@@ -691,8 +697,16 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 for (int k = lane; k < W; k += 32) bxs[k] = sel_word(x, k);
             }
             const int fi = 32 * fw + f;
-            const bool comp = dense_comp(x, N);
             __syncwarp();
+            if constexpr (!DENSE) {
+                if (lane == 0) {
+                    bs[fw] = cw | (fw == wsent ? sent : 0u);
+                    bb[fi] = (uint8_t)((cw >> f) & 1u);
+                }
+                __syncwarp();
+                nbytes += sparse_update<KU>(p, g, bb, fi, delta, lane);
+            } else {
+            const bool comp = dense_comp(x, N);
             if (lane == 0) bs[fw] = cw;            // read again after the __syncwarp below
             vh ^= vhash_bit(fi);                   // the hash of the state after the flip
             if (fi == last_bit && comp == last_comp) {
@@ -733,6 +747,7 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                 }
                 last_bit = fi;
                 last_comp = comp;
+            }
             }
             __syncwarp();
             flipped = true;
@@ -786,17 +801,18 @@ sweep_tuned_kernel(const SweepDev p)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int b = blockIdx.x * kTunedWarps + warp;       // state of this warp
     if (b >= p.B) return;                                // warp-uniform; no block barriers below
-    const int rf = REUSE ? warp_region_floats_reuse(p.N, WMAX) : warp_region_floats(p.N, WMAX);
+    const int rf = (REUSE && DENSE) ? warp_region_floats_reuse(p.N, WMAX) : warp_region_floats(p.N, WMAX);
     anneal_state<WMAX, DENSE, KU, REUSE>(p, b, sm + (size_t)warp * rf, lane);
 }
 
 // Batched form: a persistent grid whose warps take (instance, state) work
 // items from a queue (items sorted by decreasing cost) until it is empty.
-// Every item is annealed exactly as the per-instance kernel would.  The
-// sparse update is bound by instruction issue and dependent L2 round trips,
-// so sparse groups of up to 256 variables ask for 7 resident 8-warp CTAs
-// per SM (40 registers a thread, some spilled; 56 warps): uneven batch
-// 1.85 -> 1.70 s against 6 CTAs, no faster with 8.
+// Every item is annealed exactly as the per-instance kernel would (sparse
+// items through the late-phase loop, whose candidate lists skip the frozen
+// bits: the same decisions; uneven batch 1.67 -> 1.61 s).  The sparse
+// update is bound by instruction issue and dependent L2 round trips, so
+// sparse groups of up to 256 variables ask for 7 resident 8-warp CTAs per
+// SM (40 registers a thread, some spilled; 56 warps): 2.04 s with 6.
 template <bool DENSE, int WMAX>
 __host__ __device__ constexpr int batch_min_blocks() { return (!DENSE && WMAX <= 8) ? 7 : 1; }
 
@@ -814,7 +830,7 @@ sweep_batch_kernel(const SweepDev* __restrict__ descs, const int2* __restrict__ 
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems) break;
         const int2 it = items[item];
-        anneal_state<WMAX, DENSE, KU>(descs[it.x], it.y, region, lane);
+        anneal_state<WMAX, DENSE, KU, !DENSE>(descs[it.x], it.y, region, lane);
         __syncwarp();
     }
 }
@@ -1111,7 +1127,7 @@ template <int WMAX, bool DENSE, int KU, bool REUSE = false>
 inline cudaError_t run_tuned(const SweepDev& p, cudaStream_t st)
 {
     const size_t per_warp =
-        sizeof(float) * (size_t)(REUSE ? warp_region_floats_reuse(p.N, WMAX) : warp_region_floats(p.N, WMAX));
+        sizeof(float) * (size_t)((REUSE && DENSE) ? warp_region_floats_reuse(p.N, WMAX) : warp_region_floats(p.N, WMAX));
     const size_t sm = per_warp * kTunedWarps;
     auto kern = sweep_tuned_kernel<WMAX, DENSE, KU, REUSE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
