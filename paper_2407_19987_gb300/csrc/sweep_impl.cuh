@@ -720,12 +720,20 @@ __device__ __forceinline__ void anneal_state(const SweepDev& p, int b, float* g,
                     if (m) {
                         const float* e = vc + (size_t)(__ffs(m) - 1) * vcache_entry_floats(p.P);
                         const uint32_t* hd = reinterpret_cast<const uint32_t*>(e);
+                        // the vector is read together with the header that
+                        // verifies it (one round trip), used only if it does
+                        float u[WMAX];
+#pragma unroll
+                        for (int t = 0; t < WMAX; ++t) u[t] = 32 * t + lane < N ? e[16 + 32 * t + lane] : 0.0f;
                         const bool bad = lane <= W && hd[lane] != (lane == 0 ? (uint32_t)fi : sel_word(x, lane - 1));
                         if (__ballot_sync(0xffffffffu, bad) == 0u) {
-                            for (int j = lane; j < N; j += 32) {
-                                const float u = e[16 + j];
-                                g[j] = __fadd_rn(g[j], __fmul_rn(delta, u));
-                                ucache[j] = u;
+#pragma unroll
+                            for (int t = 0; t < WMAX; ++t) {
+                                const int j = 32 * t + lane;
+                                if (j < N) {
+                                    g[j] = __fadd_rn(g[j], __fmul_rn(delta, u[t]));
+                                    ucache[j] = u[t];
+                                }
                             }
                             nbytes += (int64_t)(16 + N) * 4;
                             hit = true;
