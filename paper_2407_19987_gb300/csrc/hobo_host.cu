@@ -523,8 +523,24 @@ static int build_instance(hobo_instance* h, std::vector<Entry>& mono, unsigned f
                         if (q != r) colsum[(size_t)v[q] * P + v[r]] += (double)(float)e.c;
             }
         std::vector<float> S3col(colsum.begin(), colsum.end());
+        // the sweep's slabs: slab i's N rows, then its ceil(N/2) pair rows,
+        // row q the float32 sum of rows 2q and 2q + 1 (the update reads one
+        // pair row where both bits of a pair are listed)
+        const int NS = N + (N + 1) / 2;
+        std::vector<float> S3x((size_t)N * NS * P, 0.0f);
+        for (int i = 0; i < N; ++i) {
+            const float* src = S3.data() + (size_t)i * N * P;
+            float* dst = S3x.data() + (size_t)i * NS * P;
+            std::copy(src, src + (size_t)N * P, dst);
+            for (int q = 0; 2 * q < N; ++q)
+                for (int j = 0; j < P; ++j) {
+                    const float r0 = src[(size_t)(2 * q) * P + j];
+                    const float r1 = 2 * q + 1 < N ? src[(size_t)(2 * q + 1) * P + j] : 0.0f;
+                    dst[(size_t)(N + q) * P + j] = r0 + r1;
+                }
+        }
         int rc;
-        if ((rc = upload(&d.a, a)) || (rc = upload(&d.S2, S2)) || (rc = upload(&d.S3, S3)) ||
+        if ((rc = upload(&d.a, a)) || (rc = upload(&d.S2, S2)) || (rc = upload(&d.S3, S3x)) ||
             (rc = upload(&d.S3col, S3col)))
             return rc;
 

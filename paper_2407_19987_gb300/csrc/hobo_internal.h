@@ -55,7 +55,7 @@ struct DevLayouts {
     //     float32; bf16 split planes of S3 for the tensor-core contraction.
     float* a = nullptr;
     float* S2 = nullptr;
-    float* S3 = nullptr;
+    float* S3 = nullptr;         // [N][N + ceil(N/2)][P]: slab i's rows, then its pair rows
     float* S3col = nullptr;      // [N][P]: S3col[i][j] = sum_l S3[i][l][j]
     // exact re-score of dense instances: fixed-point coefficients (scale
     // 2^fix_shift) C3fix[m][j][l] for m < j < l (else 0), S2fix[m][j] for

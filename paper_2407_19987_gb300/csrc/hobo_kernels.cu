@@ -424,15 +424,24 @@ __global__ void sweep_plain_kernel(const SweepDev p)
             const float delta = xi ? -1.0f : 1.0f;
             if (DENSE) {
                 // same sums, in the same order, as the tuned kernel
-                const float* slab = p.S3 + (int64_t)i * N * P;
+                const float* slab = p.S3 + (int64_t)i * p.NS * P;
                 int pop = 0;
                 for (int k = 0; k < W; ++k) pop += __popc(x[k]);
                 const bool comp = 2 * pop > N;
-                nbytes += (int64_t)(comp ? N - pop : pop) * P * 4 + (comp ? 2 : 1) * (int64_t)P * 4;
+                // listed bits: set (clear with comp), except i; one row per
+                // pair with a listed bit, the pair row when both are
+                auto listed = [&](int l) { return l < N && l != i && bit_of(x, l) != (comp ? 1u : 0u); };
+                int nrows = 0;
+                for (int l = 0; l < N; l += 2) nrows += (listed(l) || listed(l + 1)) ? 1 : 0;
+                nbytes += (int64_t)nrows * P * 4 + (comp ? 2 : 1) * (int64_t)P * 4;
                 for (int j = 0; j < N; ++j) {
                     float acc = 0.0f;
-                    for (int l = 0; l < N; ++l)
-                        if (bit_of(x, l) != (comp ? 1u : 0u)) acc = __fadd_rn(acc, slab[(int64_t)l * P + j]);
+                    for (int l = 0; l < N; l += 2) {
+                        const bool a0 = listed(l), a1 = listed(l + 1);
+                        if (a0 && a1) acc = __fadd_rn(acc, slab[(int64_t)(N + l / 2) * P + j]);
+                        else if (a0) acc = __fadd_rn(acc, slab[(int64_t)l * P + j]);
+                        else if (a1) acc = __fadd_rn(acc, slab[(int64_t)(l + 1) * P + j]);
+                    }
                     if (comp) acc = __fsub_rn(p.S3col[(int64_t)i * P + j], acc);
                     g[j] = __fadd_rn(g[j], __fmul_rn(delta, __fadd_rn(p.S2[(int64_t)i * P + j], acc)));
                 }
@@ -476,7 +485,7 @@ SweepDev make_dev(const hobo_instance* h, const SweepArgs& a)
 {
     SweepDev p{};
     p.N = h->N; p.W = h->W; p.B = a.B; p.sweeps = a.sweeps; p.sweep0 = a.sweep0;
-    p.resume = a.resume; p.P = (h->N + 3) & ~3;
+    p.resume = a.resume; p.P = (h->N + 3) & ~3; p.NS = h->N + (h->N + 1) / 2;
     p.k0 = (uint32_t)a.seed; p.k1 = (uint32_t)(a.seed >> 32);
     p.state0 = a.state0;
     p.beta = a.beta; p.X = a.X; p.g = a.g; p.E = a.E; p.bestX = a.bestX; p.bestE = a.bestE;

@@ -20,6 +20,7 @@ namespace hobo {
 // ===========================================================================
 struct SweepDev {
     int N, W, B, sweeps, sweep0, resume, P;   // P: row pitch of the dense slab
+    int NS;              // rows per dense slab: N rows, then ceil(N/2) pair rows
     int write_g;
     uint32_t k0, k1;
     uint32_t state0;     // global index of state 0 (Philox counter offset)
@@ -39,7 +40,7 @@ struct SweepDev {
     const uint16_t* uconds;
     const void* uent;    // packed entries (coefficient bits + conditions)
     const float* S2;     // [N][P]
-    const float* S3;     // [N][N][P]
+    const float* S3;     // [N][NS][P]: row l < N is S3[i][l], row N + q the sum of rows 2q, 2q + 1
     const float* S3col;  // [N][P] column sums of each slab
     float* vcache;       // late-phase dense sweep: [B][vslots] vector-cache entries, or null
     int vslots;          // entries per state (2..kVSlots) when vcache is set
@@ -119,7 +120,8 @@ constexpr int kTunedMinBlocks = 27;
 // Dense order<=3 update for a flip of bit i: g_j += delta * (S2[i][j] +
 // sum_{l set} S3[i][l][j]).  When more than half of the bits are set the
 // slab sum is formed as colsum[i][j] - sum_{l clear} S3[i][l][j] instead, so
-// at most N/2 rows are read.  Lanes own 4 consecutive targets in each
+// at most N/2 rows are listed; a pair of listed bits (2q, 2q + 1) is read
+// as one pre-summed pair row, so about 3/8 N rows are read.  Lanes own 4 consecutive targets in each
 // 128-wide chunk (NC chunks); rows are visited in ascending order, 8 at a
 // time with their loads in flight together.
 // Shared-memory staging of slab rows by cp.async (16 bytes per lane per
@@ -144,13 +146,15 @@ __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __rest
                                                 float* __restrict__ stage = nullptr)
 {
     const int N = p.N, P = p.P, W = p.W;
-    const float* __restrict__ slab = p.S3 + (int64_t)i * N * P;
+    const float* __restrict__ slab = p.S3 + (int64_t)i * p.NS * P;
     int pop = 0;
 #pragma unroll
     for (int k = 0; k < WMAX; ++k) pop += __popc(x[k]);
     const bool comp = 2 * pop > N;
-    // offsets (in floats, within the slab) of the rows to read, ascending:
-    // set bits, or clear bits below N
+    // the listed bits: set bits, or clear bits below N, except bit i (row i
+    // is zero); offsets (in floats, within the slab) of the rows to read, one
+    // per pair (2q, 2q + 1) with a listed bit, ascending: the pair row where
+    // both are listed, else the listed bit's row
     int nrows = 0;
 #pragma unroll
     for (int k = 0; k < WMAX; ++k) {
@@ -161,8 +165,15 @@ __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __rest
             const int rem = N - 32 * k;
             if (rem < 32) u &= (1u << rem) - 1u;
         }
-        if ((u >> lane) & 1u) rows[nrows + __popc(u & ((1u << lane) - 1u))] = (uint32_t)((32 * k + lane) * P);
-        nrows += __popc(u);
+        if (k == (i >> 5)) u &= ~(1u << (i & 31));
+        const uint32_t any = (u | (u >> 1)) & 0x55555555u;     // at the pair's even bit
+        const uint32_t both = u & (u >> 1) & 0x55555555u;
+        if ((any >> lane) & 1u) {
+            const int l = 32 * k + lane;
+            const int row = ((both >> lane) & 1u) ? N + (l >> 1) : (((u >> lane) & 1u) ? l : l + 1);
+            rows[nrows + __popc(any & ((1u << lane) - 1u))] = (uint32_t)(row * P);
+        }
+        nrows += __popc(any);
     }
     __syncwarp();
     const int64_t bytes = (int64_t)nrows * P * 4 + (comp ? 2 : 1) * (int64_t)P * 4;
@@ -272,14 +283,12 @@ __device__ __forceinline__ int64_t dense_update(const SweepDev& p, float* __rest
 }
 
 // Late-phase reuse of the update vector.  The vector of a flip of bit i,
-// u_j = S2[i][j] + (sum over the row list of S3[i][l][j]), does not depend
-// on x_i: slab i's row i is zero, so when the next accepted flip of a state
+// u_j = S2[i][j] + (sum over the row list of slab i's rows), does not depend
+// on x_i: bit i is never listed, so when the next accepted flip of a state
 // is bit i again (no other bit changed in between) and the choice between
-// set rows and clear rows is the same, its row list differs only by that
-// zero row, and adding +0 to a sum that is never -0 changes nothing.  The
-// same float vector then comes out, and the state's last vector, kept in
-// shared memory, is applied instead of reading the rows again.  With x
-// already flipped:
+// set rows and clear rows is the same, the row list and so the float vector
+// are the same, and the state's last vector, kept in shared memory, is
+// applied instead of reading the rows again.  With x already flipped:
 template <int WMAX>
 __device__ __forceinline__ bool dense_comp(const uint32_t (&x)[WMAX], int N)
 {
