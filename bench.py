@@ -511,7 +511,8 @@ def runs_for_all_99(p):
 
 
 SWEEP_SOURCES = ("paper_2407_19987_gb300/csrc/sweep_impl.cuh", "paper_2407_19987_gb300/csrc/sweep_dense.cu",
-                 "paper_2407_19987_gb300/csrc/hobo_dev.cuh", "paper_2407_19987_gb300/csrc/hobo_kernels.cu")
+                 "paper_2407_19987_gb300/csrc/hobo_dev.cuh", "paper_2407_19987_gb300/csrc/hobo_kernels.cu",
+                 "paper_2407_19987_gb300/csrc/hobo_host.cu")
 SWEEP_PROFILE = "profiles/sweep_tuned_dense_N256_B4096.md"
 
 
