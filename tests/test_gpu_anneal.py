@@ -75,6 +75,11 @@ LATE_CASES = [
     # ten words per state (N = 300)
     ("dense_int_N300", lambda: W.random_sparse(61, 300, 3, 0.3, "int", imax=2), 4, 8,
      lambda: W.geometric_betas(200.0, 0.5, 120)),
+    # odd N: the last bit has no pair partner (N = 45, and N = 289 over ten words)
+    ("dense_int_N45_odd", lambda: W.random_sparse(63, 45, 3, 0.5, "int"), 4, 48,
+     lambda: W.geometric_betas(30.0, 0.05, 200)),
+    ("dense_int_N289_odd", lambda: W.random_sparse(64, 289, 3, 0.3, "int", imax=2), 4, 8,
+     lambda: W.geometric_betas(200.0, 0.5, 60)),
 ]
 
 
@@ -89,10 +94,11 @@ def test_long_dense_anneal_matches_oracle(name, maker, flags, B, sched):
     h.close()
 
 
+@pytest.mark.parametrize("N", [96, 97])
 @pytest.mark.parametrize("sched", [lambda: W.geometric_betas(10.0, 0.01, 400), lambda: _reheat(10.0, 0.01, 400)],
                          ids=["geometric", "reheat"])
-def test_long_dense_float_anneal_tuned_equals_plain(sched):
-    inst = W.dense_float(52, 96)
+def test_long_dense_float_anneal_tuned_equals_plain(sched, N):
+    inst = W.dense_float(52, N)
     betas = sched()
     h = gpuh.make(inst)
     a = _run(h, 98, 32, betas, TUNED)
