@@ -230,7 +230,16 @@ typedef struct {
  *   accepted iff dE <= 0 or u < exp2(-(beta*dE)*log2 e), u = (w>>8)*2^-24,
  *   where exp2 is the library's fixed float sequence (range reduction to
  *   [-0.5,0.5], degree-6 Taylor polynomial; 0 below -125).  Fields are
- *   updated incrementally after each accepted flip.
+ *   updated incrementally after each accepted flip; for a dense layout the
+ *   vector added for a flip of bit i is S2[i] plus the float32 sum, in
+ *   ascending order of the pairs (2q, 2q+1), of one slab row per pair with
+ *   a listed bit (listed: the set bits other than i, or the clear ones with
+ *   colsum[i] minus their sum when more than half are set), the
+ *   pre-summed pair row where both are listed: the same floats in every
+ *   mode and launch split.
+ *   Temporaries are stream-ordered allocations on `stream` (schedule,
+ *   states, fields; for dense layouts of up to 256 variables a cache of
+ *   recent update vectors of at most 1 GiB, skipped when it cannot be had).
  *   bestX   device uint32 [B][W]: lowest-energy state seen by each state
  *           (strict improvement; in/out when opts->resume)
  *   bestE   device double [B]: energy of bestX re-scored in float64
