@@ -2,6 +2,7 @@
 // contraction (float32), float64 re-scoring, and the Metropolis sweeps
 // (tuned warp-per-state kernel and the plain thread-per-state kernel).
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 #include "hobo_internal.h"
 #include "hobo_dev.cuh"
@@ -513,6 +514,40 @@ constexpr int kSplitMin = 16;
 // Device memory the late-phase vector cache may take in one call.
 constexpr size_t kVCacheBytes = 1ull << 30;
 
+// The vector cache comes from a memory pool of the library's own on each
+// device that keeps up to kVCacheBytes between calls (the device's default
+// pool hands freed memory back at every synchronization, and mapping the
+// cache again cost each call a few hundred microseconds).  nullptr when the
+// pool cannot be made.
+static cudaMemPool_t vcache_pool()
+{
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDevices] = {};
+    static bool tried[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!tried[dev]) {
+        tried[dev] = true;
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+            uint64_t keep = kVCacheBytes;
+            (void)cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            pools[dev] = pool;
+        }
+        (void)cudaGetLastError();
+    }
+    return pools[dev];
+}
+
 cudaError_t launch_sweep_tuned(const hobo_instance* h, const SweepArgs& a, cudaStream_t st)
 {
     if (a.B == 0 || a.sweeps == 0) return cudaSuccess;
@@ -537,7 +572,8 @@ cudaError_t launch_sweep_tuned(const hobo_instance* h, const SweepArgs& a, cudaS
         if (h->W <= 8) {
             const size_t entry = sizeof(float) * (size_t)vcache_entry_floats((h->N + 3) & ~3);
             slots = (int)std::min<size_t>(kVSlots, kVCacheBytes / std::max<size_t>(1, entry * (size_t)a.B));
-            if (slots >= 2 && cudaMallocAsync((void**)&vc, entry * (size_t)a.B * slots, st) != cudaSuccess) {
+            cudaMemPool_t pool = slots >= 2 ? vcache_pool() : nullptr;
+            if (pool && cudaMallocFromPoolAsync((void**)&vc, entry * (size_t)a.B * slots, pool, st) != cudaSuccess) {
                 (void)cudaGetLastError();
                 vc = nullptr;
             }
