@@ -241,7 +241,9 @@ typedef struct {
  *   states, fields; for dense layouts of up to 256 variables a cache of
  *   recent update vectors of at most 1 GiB, skipped when it cannot be had,
  *   from a memory pool of the library's that keeps up to 1 GiB per device
- *   between calls).
+ *   between calls; the pool is made on the first dense anneal of a device
+ *   and lives as long as the process: do not call cudaDeviceReset between
+ *   anneals).
  *   bestX   device uint32 [B][W]: lowest-energy state seen by each state
  *           (strict improvement; in/out when opts->resume)
  *   bestE   device double [B]: energy of bestX re-scored in float64
