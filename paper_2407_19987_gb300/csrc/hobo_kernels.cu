@@ -518,7 +518,8 @@ constexpr size_t kVCacheBytes = 1ull << 30;
 // device that keeps up to kVCacheBytes between calls (the device's default
 // pool hands freed memory back at every synchronization, and mapping the
 // cache again cost each call a few hundred microseconds).  nullptr when the
-// pool cannot be made.
+// pool cannot be made.  The pool lives as long as the process (a device
+// reset would leave its handle stale).
 static cudaMemPool_t vcache_pool()
 {
     constexpr int kMaxDevices = 64;
